@@ -1,0 +1,176 @@
+/*
+ * gsstv.h -- C ABI of the GB300 (sm_103a) GeoSSTV P-PDS solver.
+ *
+ * The library runs Algorithm 1 of Takemoto & Ono, "GeoSSTV" (arXiv
+ * 2510.00562): the preconditioned primal-dual splitting (P-PDS) solver of the
+ * constrained denoising/destriping problem Prob. 15, rewritten as Prob. 20,
+ *
+ *   min  omega ||w1||_{1,2} + ||w2||_{1,2}
+ *   s.t. s in B_{1,alpha}, t in B_{1,beta}, D_v t = 0,
+ *        u + s + t in B_{2,eps}^v, u in [mu_lo, mu_hi],
+ *        L^T w1 = D u,  L^T w2 = D D_s u,
+ *
+ * where D = (D_v; D_h) are the spatial forward differences, D_s the spectral
+ * one (Sec. II-A, Neumann boundary) and L stacks Condat's interpolators
+ * L_vert, L_hori, L_cent band by band (Sec. II-D Eqs. 10-12, Sec. III-A
+ * Eq. 13).  The proximity operators are those of Eqs. 21-24; the l1 balls are
+ * projected exactly (Sec. III-B).
+ *
+ * Conventions shared by every entry point:
+ *  - A cube has N1 rows (vertical), N2 columns (horizontal) and N3 bands and
+ *    is a C-contiguous float32 array of shape (N3, N1, N2): element (b, i, j)
+ *    sits at offset (b*N1 + i)*N2 + j.
+ *  - Pointers named d_* are CUDA device pointers, h_* host pointers.  The
+ *    caller owns every pointer it passes; the library never frees them and
+ *    keeps none of them after the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work of a handle is issued on the handle's stream.
+ *  - Every function returns GSSTV_OK (0) or a negative GSSTV_ERR_* code; on
+ *    error the outputs are unspecified and the handle stays valid.
+ *  - One handle must not be used from two host threads at once.
+ */
+#ifndef GSSTV_H
+#define GSSTV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define GSSTV_OK              0
+#define GSSTV_ERR_ARG        -1  /* null pointer, bad shape, bad parameter    */
+#define GSSTV_ERR_OOM        -2  /* a device allocation failed                */
+#define GSSTV_ERR_CUDA       -3  /* a CUDA runtime/driver call failed         */
+#define GSSTV_ERR_NONFINITE  -4  /* NaN/Inf reached the l2-ball norm          */
+#define GSSTV_ERR_TIMEOUT    -5  /* a bounded device wait gave up             */
+#define GSSTV_ERR_INTERNAL   -6  /* an internal consistency check failed      */
+
+/* ---- storage type of the iterates (arithmetic is always float32) ------- */
+#define GSSTV_FP32  0
+#define GSSTV_BF16  1
+#define GSSTV_FP16  2
+
+/* ---- threshold search for the l1-ball projections ----------------------- */
+#define GSSTV_TAU_AUTO   0  /* windowed search around the last threshold,
+                               exact radix search when the window misses   */
+#define GSSTV_TAU_EXACT  1  /* always the exact radix search               */
+
+typedef struct gsstv_params {
+    /* Prob. 15 (Eqs. 16-19) and Eq. 13 */
+    double eps;       /* radius of the l2 ball around v, >= 0               */
+    double alpha;     /* radius of the l1 ball on s, >= 0 (0 forces s = 0)  */
+    double beta;      /* radius of the l1 ball on t, >= 0 (0 forces t = 0)  */
+    double omega;     /* weight of the first-order term, >= 0               */
+    double mu_lo;     /* box on u: mu_lo < mu_hi                            */
+    double mu_hi;
+    /* step sizes of Algorithm 1, all > 0; gsstv_default_params sets the
+       values printed in Sec. III-B (1/13, 1/4, 1/4, 1, 1/3, 1/5 x 4).      */
+    double gamma_u, gamma_w1, gamma_w2, gamma_s, gamma_t;
+    double gamma_y1, gamma_y2, gamma_y3, gamma_y4;
+    /* driver */
+    int    max_iter;     /* iterations per gsstv_solve (the cap if tol > 0)  */
+    double tol;          /* Eq. 28: stop when ||u+ - u|| / ||u|| < tol; 0 = off */
+    int    check_every;  /* iterations between two Eq. 28 tests (>= 1)       */
+    int    storage;      /* GSSTV_FP32 | GSSTV_BF16 | GSSTV_FP16             */
+    int    tau_mode;     /* GSSTV_TAU_AUTO | GSSTV_TAU_EXACT                 */
+    int    graph_iters;  /* iterations per captured CUDA graph; 0 = no graph */
+} gsstv_params;
+
+typedef struct gsstv_handle gsstv_handle;
+
+/* Per-handle counters, for benchmarks and tests. */
+typedef struct gsstv_stats {
+    int64_t iterations;        /* iterations run since create / reset_stats  */
+    int64_t tau_window_hits;   /* l1 thresholds found by the windowed search */
+    int64_t tau_exact_runs;    /* l1 thresholds found by the radix search    */
+    double  k1_ms;             /* summed duration of the fused stencil kernel
+                                  while timing is on (gsstv_set_timing)       */
+    int64_t k1_launches;       /* launches covered by k1_ms                   */
+    double  last_rel_change;   /* Eq. 28 ratio of the last iteration          */
+    double  last_tau_s, last_tau_t; /* thresholds of the last iteration      */
+    double  last_l2_scale;     /* min(1, eps / ||y4'/gamma_y4 - v||) (Eq. 23) */
+} gsstv_stats;
+
+/* Device views of the full state (float32, each a (N3,N1,N2) cube or a stack
+ * of them): w1, w2 are 6 cubes ordered (grid g, component c) with g = 0, 1, 2
+ * for the grids (i+1/2, j), (i, j+1/2), (i, j) of L_vert, L_hori, L_cent and
+ * c = 0 vertical, 1 horizontal; y1, y2 are 2 cubes (vertical, horizontal). */
+typedef struct gsstv_state_view {
+    float* u; float* s; float* t;
+    float* w1; float* w2;      /* 6*N floats each */
+    float* y1; float* y2;      /* 2*N floats each */
+    float* y3; float* y4;
+} gsstv_state_view;
+
+/* Fills *p with the printed step sizes of Sec. III-B, eps = alpha = beta = 1,
+ * omega = 0.03, box [0, 1], max_iter = 1000, tol = 0, check_every = 100,
+ * storage FP32, tau_mode AUTO, graph_iters = 16. */
+void gsstv_default_params(gsstv_params* p);
+
+/* Creates a solver for N1 x N2 x N3 cubes.  Allocates and zeroes the whole
+ * iterate state on the current device (about 43 cube-sized buffers of the
+ * storage type plus a float32 copy of v).  stream: cudaStream_t or NULL. */
+int gsstv_create(gsstv_handle** h, int n1, int n2, int n3,
+                 const gsstv_params* p, void* stream);
+
+/* Replaces the parameters (same shape and storage type). */
+int gsstv_set_params(gsstv_handle* h, const gsstv_params* p);
+
+/* Releases every resource of the handle.  NULL is accepted. */
+int gsstv_destroy(gsstv_handle* h);
+
+/* Copies the observation v (d_v, device, N floats) into the handle. */
+int gsstv_load_observation(gsstv_handle* h, const float* d_v);
+
+/* Sets the starting point of Algorithm 1: u = v, and s, t, w1, w2, y1..y4 = 0. */
+int gsstv_reset_state(gsstv_handle* h);
+
+/* Runs `n` passes of Algorithm 1 from the current state (n >= 0).  When
+ * tol > 0 it stops early once Eq. 28 holds at a check; *iters_done (may be
+ * NULL) receives the number of passes run.  Synchronises the stream only for
+ * the Eq. 28 checks and the final error check. */
+int gsstv_iterate(gsstv_handle* h, int n, int* iters_done);
+
+/* gsstv_load_observation + gsstv_reset_state + gsstv_iterate(max_iter), then
+ * copies u, s, t (device, N floats each; s and t may be NULL) out. */
+int gsstv_solve(gsstv_handle* h, const float* d_v, float* d_u, float* d_s,
+                float* d_t, int* iters_done);
+
+/* The same, end to end from host memory: copies h_v in, solves, copies u, s,
+ * t back (s, t may be NULL).  Pinned host memory gives the fastest copies. */
+int gsstv_solve_host(gsstv_handle* h, const float* h_v, float* h_u, float* h_s,
+                     float* h_t, int* iters_done);
+
+/* Reads / writes the full state through float32 device views (every pointer
+ * non-NULL).  With 16-bit storage the values are rounded on write. */
+int gsstv_get_state(gsstv_handle* h, const gsstv_state_view* st);
+int gsstv_set_state(gsstv_handle* h, const gsstv_state_view* st);
+
+/* Counters; timing adds CUDA events around each launch of the fused stencil
+ * kernel (off by default). */
+int gsstv_get_stats(gsstv_handle* h, gsstv_stats* out);
+int gsstv_reset_stats(gsstv_handle* h);
+int gsstv_set_timing(gsstv_handle* h, int on);
+
+/* Bytes the handle holds on the device. */
+int64_t gsstv_device_bytes(const gsstv_handle* h);
+
+/* Projection onto the l1 ball {z : ||z||_1 <= radius} (Sec. III-B, the prox
+ * of the indicator of B_{1,alpha}): d_out = sign(x) max(|x| - tau, 0), with
+ * tau >= 0 the root of sum max(|x_i| - tau, 0) = radius, or d_out = d_x when
+ * ||x||_1 <= radius; radius = 0 gives d_out = 0.  d_x, d_out: device, n
+ * floats (may alias); tau_out: host double (may be NULL).  Allocates its
+ * scratch with cudaMalloc and synchronises the stream before returning. */
+int gsstv_project_l1ball(const float* d_x, int64_t n, double radius,
+                         float* d_out, double* tau_out, void* stream);
+
+/* Human-readable text of a return code. */
+const char* gsstv_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSSTV_H */

@@ -1,0 +1,500 @@
+// Host driver and C ABI of libgsstv (declared in include/gsstv.h).
+//
+// One iteration of Algorithm 1 is five launches on the handle's stream:
+//   K1  fused stencil pass (u, w1, w2, y1, y2 and the l1 window statistics);
+//   R0, R1, R2  radix passes of the exact l1-threshold search (each returns at
+//       once unless the previous step left that level pending);
+//   G   gather of the bracket bin (same early return);
+//   K2  light pass (s, t, y3, y4 and the l2-ball norm).
+// Every scalar that couples the iteration (the thresholds tau_s, tau_t and the
+// l2-ball scale c) stays on the device, so a block of iterations can be
+// captured once into a CUDA graph and replayed; the host synchronises only
+// for the stopping rule (Eq. 28) and for the final error check.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gsstv.h"
+#include "gsstv_internal.cuh"
+
+using namespace gsstv;
+
+struct gsstv_handle {
+    Geom g{};
+    gsstv_params p{};
+    cudaStream_t st = nullptr;
+    int esz = 4;
+    void *u[2]{}, *s[2]{}, *t[2]{}, *y3[2]{}, *q[2]{};
+    void *w1[2]{}, *w2[2]{}, *y1[2]{}, *y2[2]{};
+    float* v = nullptr;
+    float* tmp = nullptr;         // dense float32 scratch for host copies (16-bit storage)
+    Scal* sc = nullptr;
+    L1Work l1{};
+    double* k2_part = nullptr;
+    int k2_cap = 0;
+    int k1_ctas = 0;
+    int parity = 0;               // ping-pong index that holds the current state
+    cudaGraphExec_t gexec[2]{};
+    int graph_len = 0;
+    int timing = 0;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    gsstv_stats stats{};
+    int64_t bytes = 0;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? GSSTV_OK : GSSTV_ERR_CUDA; }
+#define TRY(x) do { int rc__ = (x); if (rc__ != GSSTV_OK) return rc__; } while (0)
+
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int check_params(const gsstv_params* p) {
+    if (!p) return GSSTV_ERR_ARG;
+    if (!finite_nonneg(p->eps) || !finite_nonneg(p->alpha) || !finite_nonneg(p->beta) || !finite_nonneg(p->omega))
+        return GSSTV_ERR_ARG;
+    if (!std::isfinite(p->mu_lo) || !std::isfinite(p->mu_hi) || !(p->mu_lo < p->mu_hi)) return GSSTV_ERR_ARG;
+    const double gam[] = {p->gamma_u, p->gamma_w1, p->gamma_w2, p->gamma_s, p->gamma_t,
+                          p->gamma_y1, p->gamma_y2, p->gamma_y3, p->gamma_y4};
+    for (double x : gam)
+        if (!finite_pos(x)) return GSSTV_ERR_ARG;
+    if (p->max_iter < 0 || p->check_every < 1 || p->graph_iters < 0) return GSSTV_ERR_ARG;
+    if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return GSSTV_ERR_ARG;
+    if (p->storage < GSSTV_FP32 || p->storage > GSSTV_FP16) return GSSTV_ERR_ARG;
+    if (p->tau_mode != GSSTV_TAU_AUTO && p->tau_mode != GSSTV_TAU_EXACT) return GSSTV_ERR_ARG;
+    return GSSTV_OK;
+}
+
+int dalloc(gsstv_handle* h, void** out, size_t bytes) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(out, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return GSSTV_ERR_OOM;
+    }
+    h->allocs.push_back(*out);
+    h->bytes += (int64_t)bytes;
+    if (cudaMemsetAsync(*out, 0, bytes, h->st) != cudaSuccess) return GSSTV_ERR_CUDA;
+    return GSSTV_OK;
+}
+
+void free_all(gsstv_handle* h) {
+    for (int k = 0; k < 2; ++k)
+        if (h->gexec[k]) { cudaGraphExecDestroy(h->gexec[k]); h->gexec[k] = nullptr; }
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+    if (h->st) cudaStreamSynchronize(h->st);
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+void destroy_graphs(gsstv_handle* h) {
+    for (int k = 0; k < 2; ++k)
+        if (h->gexec[k]) { cudaGraphExecDestroy(h->gexec[k]); h->gexec[k] = nullptr; }
+    h->graph_len = 0;
+}
+
+IterBufs bufs(const gsstv_handle* h, int par) {
+    const int n = par ^ 1;
+    IterBufs b;
+    b.u = h->u[par]; b.s = h->s[par]; b.t = h->t[par]; b.y3 = h->y3[par]; b.q = h->q[par];
+    b.w1 = h->w1[par]; b.w2 = h->w2[par]; b.y1 = h->y1[par]; b.y2 = h->y2[par];
+    b.u_n = h->u[n]; b.s_n = h->s[n]; b.t_n = h->t[n]; b.y3_n = h->y3[n]; b.q_n = h->q[n];
+    b.w1_n = h->w1[n]; b.w2_n = h->w2[n]; b.y1_n = h->y1[n]; b.y2_n = h->y2[n];
+    b.v = h->v;
+    return b;
+}
+
+IterParams iparams(const gsstv_handle* h, int par) {
+    const gsstv_params& p = h->p;
+    IterParams ip;
+    ip.gamma_u = (float)p.gamma_u; ip.gamma_w1 = (float)p.gamma_w1; ip.gamma_w2 = (float)p.gamma_w2;
+    ip.gamma_s = (float)p.gamma_s; ip.gamma_t = (float)p.gamma_t;
+    ip.gamma_y1 = (float)p.gamma_y1; ip.gamma_y2 = (float)p.gamma_y2;
+    ip.gamma_y3 = (float)p.gamma_y3; ip.gamma_y4 = (float)p.gamma_y4;
+    ip.thr_w1 = (float)(p.gamma_w1 * p.omega);
+    ip.thr_w2 = (float)p.gamma_w2;
+    ip.mu_lo = (float)p.mu_lo; ip.mu_hi = (float)p.mu_hi;
+    ip.eps = p.eps;
+    ip.parity = par;
+    ip.tau_exact = p.tau_mode == GSSTV_TAU_EXACT;
+    return ip;
+}
+
+int map_launch(int rc) { return rc == 0 ? GSSTV_OK : rc == -1 ? GSSTV_ERR_ARG : GSSTV_ERR_CUDA; }
+
+// One iteration from parity `par` (reads buffers par, writes par ^ 1).
+int enqueue_iteration(gsstv_handle* h, int par, bool timed) {
+    const IterBufs b = bufs(h, par);
+    const IterParams ip = iparams(h, par);
+    const int sto = h->p.storage;
+    if (timed) {
+        if (h->ev_used + 2 > (int)h->ev.size()) return GSSTV_ERR_INTERNAL;
+        TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used], h->st)));
+    }
+    TRY(map_launch(launch_k1(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, h->st)));
+    if (timed) {
+        TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used + 1], h->st)));
+        h->ev_used += 2;
+    }
+    for (int level = 0; level < 3; ++level)
+        TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, h->st)));
+    TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, h->st)));
+    TRY(map_launch(launch_k2(sto, h->g, b, ip, h->sc, h->k2_part, h->k2_cap, h->st)));
+    return GSSTV_OK;
+}
+
+int build_graph(gsstv_handle* h, int par, int len) {
+    cudaGraph_t graph = nullptr;
+    TRY(cuda_rc(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal)));
+    int rc = GSSTV_OK;
+    int p = par;
+    for (int k = 0; k < len && rc == GSSTV_OK; ++k) {
+        rc = enqueue_iteration(h, p, false);
+        p ^= 1;
+    }
+    cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+    if (rc != GSSTV_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return GSSTV_ERR_CUDA;
+    e = cudaGraphInstantiate(&h->gexec[par], graph, 0);
+    cudaGraphDestroy(graph);
+    return cuda_rc(e);
+}
+
+int flush_timing(gsstv_handle* h) {
+    if (h->ev_used == 0) return GSSTV_OK;
+    TRY(cuda_rc(cudaStreamSynchronize(h->st)));
+    for (int k = 0; k + 1 < h->ev_used; k += 2) {
+        float ms = 0.f;
+        TRY(cuda_rc(cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1])));
+        h->stats.k1_ms += ms;
+        h->stats.k1_launches++;
+    }
+    h->ev_used = 0;
+    return GSSTV_OK;
+}
+
+// n iterations, no stopping test
+int run_block(gsstv_handle* h, int n) {
+    const int G = h->p.graph_iters > 0 ? ((h->p.graph_iters + 1) / 2) * 2 : 0;   // even: parity returns
+    while (n > 0) {
+        if (!h->timing && G > 0 && n >= G) {
+            if (h->graph_len != G) destroy_graphs(h);
+            if (!h->gexec[h->parity]) TRY(build_graph(h, h->parity, G));
+            h->graph_len = G;
+            TRY(cuda_rc(cudaGraphLaunch(h->gexec[h->parity], h->st)));
+            n -= G;
+            h->stats.iterations += G;
+        } else {
+            if (h->timing && h->ev_used + 2 > (int)h->ev.size()) TRY(flush_timing(h));
+            TRY(enqueue_iteration(h, h->parity, h->timing != 0));
+            h->parity ^= 1;
+            --n;
+            h->stats.iterations += 1;
+        }
+    }
+    return GSSTV_OK;
+}
+
+int read_scalars(gsstv_handle* h, Scal* out) {
+    TRY(cuda_rc(cudaMemcpyAsync(out, h->sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st)));
+    return cuda_rc(cudaStreamSynchronize(h->st));
+}
+
+int error_of(const Scal& s) {
+    if (s.error & 1) return GSSTV_ERR_NONFINITE;
+    if (s.error) return GSSTV_ERR_INTERNAL;
+    return GSSTV_OK;
+}
+
+Scal initial_scalars(const gsstv_params& p) {
+    Scal s;
+    std::memset(&s, 0, sizeof(s));
+    s.radius[0] = p.alpha;
+    s.radius[1] = p.beta;
+    for (int v = 0; v < 2; ++v) {
+        s.ctl[v].window_ok = 1;       // first window (0, 0]: is the vector inside the ball?
+        s.ctl[v].need = NEED_NONE;
+    }
+    return s;
+}
+
+int upload_scalars(gsstv_handle* h, const Scal& s) {
+    Scal tmp = s;
+    TRY(cuda_rc(cudaMemcpyAsync(h->sc, &tmp, sizeof(Scal), cudaMemcpyHostToDevice, h->st)));
+    return cuda_rc(cudaStreamSynchronize(h->st));
+}
+
+}  // namespace
+
+extern "C" {
+
+void gsstv_default_params(gsstv_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->eps = 1.0; p->alpha = 1.0; p->beta = 1.0; p->omega = 0.03;
+    p->mu_lo = 0.0; p->mu_hi = 1.0;
+    p->gamma_u = 1.0 / 13.0; p->gamma_w1 = 0.25; p->gamma_w2 = 0.25;
+    p->gamma_s = 1.0; p->gamma_t = 1.0 / 3.0;
+    p->gamma_y1 = p->gamma_y2 = p->gamma_y3 = p->gamma_y4 = 0.2;
+    p->max_iter = 1000; p->tol = 0.0; p->check_every = 100;
+    p->storage = GSSTV_FP32; p->tau_mode = GSSTV_TAU_AUTO; p->graph_iters = 16;
+}
+
+int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params* p, void* stream) {
+    if (!out) return GSSTV_ERR_ARG;
+    *out = nullptr;
+    if (n1 < 1 || n2 < 1 || n3 < 1 || n1 > (1 << 20) || n2 > (1 << 20) || n3 > (1 << 16)) return GSSTV_ERR_ARG;
+    TRY(check_params(p));
+    gsstv_handle* h = new gsstv_handle();
+    h->p = *p;
+    h->st = (cudaStream_t)stream;
+    h->esz = p->storage == GSSTV_FP32 ? 4 : 2;
+    h->g.n1 = n1; h->g.n2 = n2; h->g.n3 = n3;
+    h->g.p2 = ((n2 + 7) / 8) * 8;
+    h->g.cube = (long long)n3 * n1 * h->g.p2;
+    const size_t cb = (size_t)h->g.cube * h->esz;
+    int rc = GSSTV_OK;
+    for (int k = 0; k < 2 && rc == GSSTV_OK; ++k) {
+        void** one[] = {&h->u[k], &h->s[k], &h->t[k], &h->y3[k], &h->q[k]};
+        for (void** pp : one) if (rc == GSSTV_OK) rc = dalloc(h, pp, cb);
+        if (rc == GSSTV_OK) rc = dalloc(h, &h->w1[k], 6 * cb);
+        if (rc == GSSTV_OK) rc = dalloc(h, &h->w2[k], 6 * cb);
+        if (rc == GSSTV_OK) rc = dalloc(h, &h->y1[k], 2 * cb);
+        if (rc == GSSTV_OK) rc = dalloc(h, &h->y2[k], 2 * cb);
+    }
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->v, (size_t)h->g.cube * sizeof(float));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->sc, sizeof(Scal));
+    if (rc == GSSTV_OK && (k1_configure(p->storage) != 0 || light_configure(p->storage) != 0)) rc = GSSTV_ERR_CUDA;
+    h->k1_ctas = k1_grid_ctas(h->g);
+    h->k2_cap = k2_grid_ctas(h->g);
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.cand[0], kCandCap * sizeof(float));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.cand[1], kCandCap * sizeof(float));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.hcnt, 2 * kHistBins * sizeof(unsigned long long));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.hres, 2 * kHistBins * sizeof(unsigned long long));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.k1_n, 2 * (size_t)h->k1_ctas * sizeof(unsigned long long));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.k1_s, 2 * (size_t)h->k1_ctas * sizeof(double));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->k2_part, 3 * (size_t)h->k2_cap * sizeof(double));
+    if (rc == GSSTV_OK) {
+        h->ev.resize(512);
+        for (auto& e : h->ev)
+            if (rc == GSSTV_OK && cudaEventCreate(&e) != cudaSuccess) { e = nullptr; rc = GSSTV_ERR_CUDA; }
+    }
+    if (rc == GSSTV_OK) rc = upload_scalars(h, initial_scalars(h->p));
+    if (rc != GSSTV_OK) {
+        for (auto& e : h->ev) if (e) cudaEventDestroy(e);
+        h->ev.clear();
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return GSSTV_OK;
+}
+
+int gsstv_set_params(gsstv_handle* h, const gsstv_params* p) {
+    if (!h) return GSSTV_ERR_ARG;
+    TRY(check_params(p));
+    if (p->storage != h->p.storage) return GSSTV_ERR_ARG;
+    h->p = *p;
+    destroy_graphs(h);
+    double r[2] = {p->alpha, p->beta};
+    TRY(cuda_rc(cudaMemcpyAsync(&h->sc->radius[0], r, sizeof(r), cudaMemcpyHostToDevice, h->st)));
+    return cuda_rc(cudaStreamSynchronize(h->st));
+}
+
+int gsstv_destroy(gsstv_handle* h) {
+    if (!h) return GSSTV_OK;
+    free_all(h);
+    delete h;
+    return GSSTV_OK;
+}
+
+int gsstv_load_observation(gsstv_handle* h, const float* d_v) {
+    if (!h || !d_v) return GSSTV_ERR_ARG;
+    const Geom& g = h->g;
+    return cuda_rc(cudaMemcpy2DAsync(h->v, (size_t)g.p2 * 4, d_v, (size_t)g.n2 * 4, (size_t)g.n2 * 4,
+                                     (size_t)g.n3 * g.n1, cudaMemcpyDeviceToDevice, h->st));
+}
+
+int gsstv_reset_state(gsstv_handle* h) {
+    if (!h) return GSSTV_ERR_ARG;
+    const size_t cb = (size_t)h->g.cube * h->esz;
+    for (int k = 0; k < 2; ++k) {
+        void* one[] = {h->u[k], h->s[k], h->t[k], h->y3[k], h->q[k]};
+        for (void* pp : one) TRY(cuda_rc(cudaMemsetAsync(pp, 0, cb, h->st)));
+        TRY(cuda_rc(cudaMemsetAsync(h->w1[k], 0, 6 * cb, h->st)));
+        TRY(cuda_rc(cudaMemsetAsync(h->w2[k], 0, 6 * cb, h->st)));
+        TRY(cuda_rc(cudaMemsetAsync(h->y1[k], 0, 2 * cb, h->st)));
+        TRY(cuda_rc(cudaMemsetAsync(h->y2[k], 0, 2 * cb, h->st)));
+    }
+    TRY(map_launch(launch_pitched_to_storage(h->p.storage, h->v, h->u[0], h->g, h->st)));
+    h->parity = 0;
+    return upload_scalars(h, initial_scalars(h->p));
+}
+
+int gsstv_iterate(gsstv_handle* h, int n, int* iters_done) {
+    if (!h || n < 0) return GSSTV_ERR_ARG;
+    if (iters_done) *iters_done = 0;
+    int done = 0;
+    Scal s;
+    if (h->p.tol > 0.0) {
+        while (done < n) {
+            const int blk = std::min(h->p.check_every, n - done);
+            TRY(run_block(h, blk));
+            done += blk;
+            TRY(flush_timing(h));
+            TRY(read_scalars(h, &s));
+            TRY(error_of(s));
+            h->stats.last_rel_change = s.u2 > 0 ? std::sqrt(s.du2 / s.u2) : INFINITY;
+            if (s.u2 > 0 && std::sqrt(s.du2 / s.u2) < h->p.tol) break;
+        }
+    } else {
+        TRY(run_block(h, n));
+        done = n;
+        TRY(flush_timing(h));
+        TRY(read_scalars(h, &s));
+        TRY(error_of(s));
+        h->stats.last_rel_change = s.u2 > 0 ? std::sqrt(s.du2 / s.u2) : INFINITY;
+    }
+    h->stats.last_tau_s = s.ctl[0].tau;
+    h->stats.last_tau_t = s.ctl[1].tau;
+    h->stats.last_l2_scale = s.c[h->parity];
+    if (iters_done) *iters_done = done;
+    return GSSTV_OK;
+}
+
+static int copy_out_device(gsstv_handle* h, float* d_u, float* d_s, float* d_t) {
+    const int par = h->parity;
+    if (d_u) TRY(map_launch(launch_unpack(h->p.storage, h->u[par], d_u, h->g, 1, h->st)));
+    if (d_s) TRY(map_launch(launch_unpack(h->p.storage, h->s[par], d_s, h->g, 1, h->st)));
+    if (d_t) TRY(map_launch(launch_unpack(h->p.storage, h->t[par], d_t, h->g, 1, h->st)));
+    return cuda_rc(cudaStreamSynchronize(h->st));
+}
+
+int gsstv_solve(gsstv_handle* h, const float* d_v, float* d_u, float* d_s, float* d_t, int* iters_done) {
+    if (!h || !d_v || !d_u) return GSSTV_ERR_ARG;
+    TRY(gsstv_load_observation(h, d_v));
+    TRY(gsstv_reset_state(h));
+    TRY(gsstv_iterate(h, h->p.max_iter, iters_done));
+    return copy_out_device(h, d_u, d_s, d_t);
+}
+
+int gsstv_solve_host(gsstv_handle* h, const float* h_v, float* h_u, float* h_s, float* h_t, int* iters_done) {
+    if (!h || !h_v || !h_u) return GSSTV_ERR_ARG;
+    const Geom& g = h->g;
+    const size_t w = (size_t)g.n2 * 4, dp = (size_t)g.p2 * 4, rows = (size_t)g.n3 * g.n1;
+    TRY(cuda_rc(cudaMemcpy2DAsync(h->v, dp, h_v, w, w, rows, cudaMemcpyHostToDevice, h->st)));
+    TRY(gsstv_reset_state(h));
+    TRY(gsstv_iterate(h, h->p.max_iter, iters_done));
+    const int par = h->parity;
+    void* src[3] = {h->u[par], h->s[par], h->t[par]};
+    float* dst[3] = {h_u, h_s, h_t};
+    if (h->p.storage != GSSTV_FP32 && !h->tmp) {
+        void* t = nullptr;
+        TRY(dalloc(h, &t, (size_t)g.n3 * g.n1 * g.n2 * 4));
+        h->tmp = (float*)t;
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (!dst[k]) continue;
+        if (h->p.storage == GSSTV_FP32) {
+            TRY(cuda_rc(cudaMemcpy2DAsync(dst[k], w, src[k], dp, w, rows, cudaMemcpyDeviceToHost, h->st)));
+        } else {
+            TRY(map_launch(launch_unpack(h->p.storage, src[k], h->tmp, g, 1, h->st)));
+            TRY(cuda_rc(cudaMemcpyAsync(dst[k], h->tmp, w * rows, cudaMemcpyDeviceToHost, h->st)));
+        }
+    }
+    return cuda_rc(cudaStreamSynchronize(h->st));
+}
+
+int gsstv_get_state(gsstv_handle* h, const gsstv_state_view* v) {
+    if (!h || !v || !v->u || !v->s || !v->t || !v->w1 || !v->w2 || !v->y1 || !v->y2 || !v->y3 || !v->y4)
+        return GSSTV_ERR_ARG;
+    const int par = h->parity, sto = h->p.storage;
+    TRY(map_launch(launch_unpack(sto, h->u[par], v->u, h->g, 1, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->s[par], v->s, h->g, 1, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->t[par], v->t, h->g, 1, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->w1[par], v->w1, h->g, 6, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->w2[par], v->w2, h->g, 6, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->y1[par], v->y1, h->g, 2, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->y2[par], v->y2, h->g, 2, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->y3[par], v->y3, h->g, 1, h->st)));
+    TRY(map_launch(launch_scale_unpack(sto, h->q[par], &h->sc->c[par], v->y4, h->g, h->st)));
+    return cuda_rc(cudaStreamSynchronize(h->st));
+}
+
+int gsstv_set_state(gsstv_handle* h, const gsstv_state_view* v) {
+    if (!h || !v || !v->u || !v->s || !v->t || !v->w1 || !v->w2 || !v->y1 || !v->y2 || !v->y3 || !v->y4)
+        return GSSTV_ERR_ARG;
+    const int par = h->parity, sto = h->p.storage;
+    TRY(map_launch(launch_pack(sto, v->u, h->u[par], h->g, 1, h->st)));
+    TRY(map_launch(launch_pack(sto, v->s, h->s[par], h->g, 1, h->st)));
+    TRY(map_launch(launch_pack(sto, v->t, h->t[par], h->g, 1, h->st)));
+    TRY(map_launch(launch_pack(sto, v->w1, h->w1[par], h->g, 6, h->st)));
+    TRY(map_launch(launch_pack(sto, v->w2, h->w2[par], h->g, 6, h->st)));
+    TRY(map_launch(launch_pack(sto, v->y1, h->y1[par], h->g, 2, h->st)));
+    TRY(map_launch(launch_pack(sto, v->y2, h->y2[par], h->g, 2, h->st)));
+    TRY(map_launch(launch_pack(sto, v->y3, h->y3[par], h->g, 1, h->st)));
+    TRY(map_launch(launch_pack(sto, v->y4, h->q[par], h->g, 1, h->st)));
+    // y4 is now stored unscaled (c = 0); the threshold search starts afresh
+    return upload_scalars(h, initial_scalars(h->p));
+}
+
+int gsstv_get_stats(gsstv_handle* h, gsstv_stats* out) {
+    if (!h || !out) return GSSTV_ERR_ARG;
+    TRY(flush_timing(h));
+    Scal s;
+    TRY(read_scalars(h, &s));
+    *out = h->stats;
+    out->tau_window_hits = s.ctl[0].hits + s.ctl[1].hits;
+    out->tau_exact_runs = s.ctl[0].exact_runs + s.ctl[1].exact_runs;
+    return GSSTV_OK;
+}
+
+int gsstv_reset_stats(gsstv_handle* h) {
+    if (!h) return GSSTV_ERR_ARG;
+    TRY(flush_timing(h));
+    h->stats = gsstv_stats{};
+    Scal s;
+    TRY(read_scalars(h, &s));
+    for (int v = 0; v < 2; ++v) { s.ctl[v].hits = 0; s.ctl[v].exact_runs = 0; }
+    return upload_scalars(h, s);
+}
+
+int gsstv_set_timing(gsstv_handle* h, int on) {
+    if (!h) return GSSTV_ERR_ARG;
+    TRY(flush_timing(h));
+    h->timing = on ? 1 : 0;
+    return GSSTV_OK;
+}
+
+int64_t gsstv_device_bytes(const gsstv_handle* h) { return h ? h->bytes : 0; }
+
+int gsstv_project_l1ball(const float* d_x, int64_t n, double radius, float* d_out, double* tau_out,
+                         void* stream) {
+    if (!d_x || !d_out || n < 0 || !(radius >= 0.0) || !std::isfinite(radius)) return GSSTV_ERR_ARG;
+    if (n == 0) { if (tau_out) *tau_out = 0.0; return GSSTV_OK; }
+    const int rc = l1_project_standalone(d_x, (long long)n, radius, d_out, tau_out, (cudaStream_t)stream);
+    return rc == 0 ? GSSTV_OK : rc == -2 ? GSSTV_ERR_OOM : rc == -6 ? GSSTV_ERR_INTERNAL : GSSTV_ERR_CUDA;
+}
+
+const char* gsstv_strerror(int code) {
+    switch (code) {
+        case GSSTV_OK: return "ok";
+        case GSSTV_ERR_ARG: return "invalid argument";
+        case GSSTV_ERR_OOM: return "device allocation failed";
+        case GSSTV_ERR_CUDA: return "CUDA call failed";
+        case GSSTV_ERR_NONFINITE: return "non-finite value in the l2-ball norm";
+        case GSSTV_ERR_TIMEOUT: return "bounded device wait timed out";
+        case GSSTV_ERR_INTERNAL: return "internal consistency check failed";
+    }
+    return "unknown error code";
+}
+
+}  // extern "C"

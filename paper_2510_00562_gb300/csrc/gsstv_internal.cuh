@@ -1,0 +1,250 @@
+// Internal definitions shared by the CUDA translation units of libgsstv.
+//
+// Device layout of one handle (all cubes pitched: element (b, i, j) of a cube
+// at offset (b*N1 + i)*P2 + j, P2 = N2 rounded up to 8 so every row starts on
+// a 16-byte boundary; the padding columns hold zeros and are never read as
+// data):
+//   u[2], s[2], t[2], y3[2], q[2]      one cube each, ping-pong by iteration
+//   w1[2], w2[2]                       6 cubes each (grid g, component c)
+//   y1[2], y2[2]                       2 cubes each (vertical, horizontal)
+//   v                                  float32 observation
+// y4 is kept as q with a scalar c: y4 = (1 - c) q (the l2-ball step of
+// Algorithm 1 is a global rescale, Eq. 23 with Moreau's identity Eq. 3), so
+// the scale is applied when y4 is next read instead of in an extra pass.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace gsstv {
+
+// ---------------------------------------------------------------------------
+// storage types: iterates are stored as T, every arithmetic step is float32
+// ---------------------------------------------------------------------------
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float x) { *p = x; }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half* p, float x) { *p = __float2half_rn(x); }
+};
+template <typename T> __device__ __forceinline__ float ldT(const T* p) { return Store<T>::ld(p); }
+template <typename T> __device__ __forceinline__ void stT(T* p, float x) { Store<T>::st(p, x); }
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+struct Geom {
+    int n1, n2, n3;   // rows, columns, bands
+    int p2;           // row pitch in elements (multiple of 8)
+    long long cube;   // elements of one pitched cube = n3 * n1 * p2
+    __host__ __device__ __forceinline__ long long at(int b, int i, int j) const {
+        return ((long long)b * n1 + i) * p2 + j;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// l1-ball threshold search state (one per projected vector: 0 = s, 1 = t)
+// ---------------------------------------------------------------------------
+enum L1Need : int {
+    NEED_NONE = 0,      // tau of this iteration is known
+    NEED_RADIX0 = 1,    // run the radix histogram, level 0 (bits 30..20)
+    NEED_RADIX1 = 2,    // level 1 (bits 19..9) inside the level-0 bin
+    NEED_RADIX2 = 3,    // level 2 (bits 8..0): single-value bins
+    NEED_GATHER = 4,    // gather the bracket bin and finish with Michelot steps
+};
+
+struct L1Ctl {
+    float theta_lo, theta_hi;  // window (theta_lo, theta_hi] for the next pass
+    int window_ok;             // 1: K1 accumulates window statistics
+    int need;                  // L1Need
+    double tau;                // threshold of the current iteration
+    double tau_prev;           // threshold of the previous iteration
+    int have_tau, have_prev;
+    double dens;               // candidates per unit of |x| at the last window
+    // radix search
+    unsigned prefix;           // key bits fixed by the previous levels
+    unsigned long long n_above;// elements above the current bracket (exact)
+    double s_above;            // their sum (exact up to double rounding)
+    float g_lo, g_hi;          // gather window (g_lo, g_hi]
+    long long hits, exact_runs;
+};
+
+struct L1Acc {
+    unsigned long long n_hi;   // elements with |x| > theta_hi
+    double s_hi;               // their sum
+    unsigned int m;            // candidates appended (may exceed the capacity)
+    unsigned int pad;
+};
+
+struct Scal {
+    double c[2];               // y4 = (1 - c[p]) q at iteration parity p
+    L1Ctl ctl[2];
+    L1Acc acc[2];
+    double radius[2];          // alpha, beta
+    unsigned int k1_ticket, k2_ticket, fb_ticket, g_ticket;
+    int error;                 // bit 0: non-finite norm; bit 1: internal
+    int pad0;
+    double q2, du2, u2;        // norms of the last K2 pass
+    long long iter;
+};
+
+constexpr int kHistBins = 2048;        // radix histogram bins per vector
+constexpr unsigned kCandCap = 1u << 20; // candidate capacity per vector
+constexpr double kCandTarget = 8192.0;  // window sized for about this many candidates
+
+// Device workspace of the l1 machinery (shared layout with the standalone
+// projection entry point).
+struct L1Work {
+    float* cand[2];                    // kCandCap floats each
+    unsigned long long* hcnt;          // [2][kHistBins]
+    unsigned long long* hres;          // [2][kHistBins]
+    unsigned long long* k1_n;          // per K1 CTA: [2] counts
+    double* k1_s;                      // per K1 CTA: [2] sums
+};
+
+// ---------------------------------------------------------------------------
+// small numerics helpers
+// ---------------------------------------------------------------------------
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Sum over the block; every thread gets the result.  `buf` holds >= 32 values.
+template <typename V>
+__device__ __forceinline__ V block_sum(V x, V* buf) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    x = warp_sum(x);
+    __syncthreads();
+    if (lane == 0) buf[wid] = x;
+    __syncthreads();
+    V r = (threadIdx.x < (unsigned)nw) ? buf[threadIdx.x] : V(0);
+    if (wid == 0) r = warp_sum(r);
+    if (threadIdx.x == 0) buf[0] = r;
+    __syncthreads();
+    r = buf[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ float soft(float x, float tau) {
+    float a = fabsf(x) - tau;
+    return a > 0.f ? copysignf(a, x) : 0.f;
+}
+
+// value of a non-negative float given by its bit pattern, and the size of
+// one unit of its last mantissa bit (as double, both exact)
+__device__ __forceinline__ double key_value(unsigned key) { return (double)__uint_as_float(key); }
+__device__ __forceinline__ double key_ulp(unsigned key) {
+    unsigned e = (key >> 23) & 0xffu;
+    return ldexp(1.0, (e == 0 ? 1 : (int)e) - 150);
+}
+
+// s~ = s - g_s y4 and t~ = t - g_t (D_v^T y3 + y4) of one voxel (the inputs of
+// the two l1-ball projections of Algorithm 1), with y4 = cs * q.  Written with
+// explicit roundings so that every kernel that needs them (the stencil pass,
+// the radix search and the light pass) computes bit-identical values.
+__device__ __forceinline__ void s_t_tilde(float s, float t, float y3, float y3_up, float q, float cs,
+                                          int i, int n1, float gs, float gt, float& xs, float& xt) {
+    const float y4 = __fmul_rn(cs, q);
+    xs = __fsub_rn(s, __fmul_rn(gs, y4));
+    const float dvt = __fsub_rn(y3_up, i <= n1 - 2 ? y3 : 0.f);
+    xt = __fsub_rn(t, __fmul_rn(gt, __fadd_rn(dvt, y4)));
+}
+
+// ---------------------------------------------------------------------------
+// window accounting for one |x| value, used by K1 and by the gather pass
+// ---------------------------------------------------------------------------
+struct WinAcc {
+    unsigned long long n = 0;
+    Kahan s;
+};
+
+// Appends the lanes' candidates with one atomic per warp.
+__device__ __forceinline__ void append_candidate(bool take, float x, float* cand, unsigned* cnt) {
+    unsigned mask = __ballot_sync(0xffffffffu, take);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (take) {
+        unsigned k = base + __popc(mask & ((1u << lane) - 1u));
+        if (k < kCandCap) cand[k] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (host)
+// ---------------------------------------------------------------------------
+struct IterBufs {
+    // current (read) and next (write) buffers of one iteration parity
+    const void *u, *s, *t, *y3, *q, *w1, *w2, *y1, *y2;
+    void *u_n, *s_n, *t_n, *y3_n, *q_n, *w1_n, *w2_n, *y1_n, *y2_n;
+    const float* v;
+};
+
+struct IterParams {
+    float gamma_u, gamma_w1, gamma_w2, gamma_s, gamma_t;
+    float gamma_y1, gamma_y2, gamma_y3, gamma_y4;
+    float thr_w1, thr_w2;        // gamma_w1 * omega, gamma_w2
+    float mu_lo, mu_hi;
+    double eps;
+    int parity;                  // iteration parity (selects c[])
+    int tau_exact;               // 1: skip the window statistics
+};
+
+int launch_k1(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
+              const L1Work& w, int n_cta_slots, cudaStream_t st);
+int k1_grid_ctas(const Geom& g);
+int k1_configure(int storage);
+int light_configure(int storage);
+int launch_fallback(int storage, int level, const Geom& g, const IterBufs& b, const IterParams& p,
+                    Scal* sc, const L1Work& w, cudaStream_t st);
+int launch_gather(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
+                  const L1Work& w, cudaStream_t st);
+int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
+              double* part, int part_cap, cudaStream_t st);
+int k2_grid_ctas(const Geom& g);
+
+// state conversion (float32 views <-> pitched storage)
+int launch_pack(int storage, const float* src, void* dst, const Geom& g, int ncubes, cudaStream_t st);
+int launch_pitched_to_storage(int storage, const float* src, void* dst, const Geom& g, cudaStream_t st);
+int launch_dense_to_pitched(const float* src, float* dst, const Geom& g, cudaStream_t st);
+int launch_unpack(int storage, const void* src, float* dst, const Geom& g, int ncubes, cudaStream_t st);
+int launch_scale_unpack(int storage, const void* q, const double* c, float* dst, const Geom& g,
+                        cudaStream_t st);
+
+// standalone projection
+int l1_project_standalone(const float* x, long long n, double radius, float* out, double* tau,
+                          cudaStream_t st);
+
+}  // namespace gsstv

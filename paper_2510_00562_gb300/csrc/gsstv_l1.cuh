@@ -1,0 +1,217 @@
+// Exact threshold of the l1-ball projection (Sec. III-B) on the GPU.
+//
+// For x in R^n and radius r > 0 with ||x||_1 > r, the projection onto
+// B_{1,r} is sign(x) max(|x| - tau, 0) where tau > 0 is the root of
+//   phi(tau) = sum_i max(|x_i| - tau, 0) - r,
+// a continuous, piecewise-linear, non-increasing function of tau.  Two ways
+// to get tau, both exact up to floating-point rounding of the sums:
+//
+//  * window: given counts and sums of the |x| above a window (lo, hi] and the
+//    values inside it (the candidates), Michelot's fixed point
+//    tau <- (sum_{|x| > tau} |x| - r) / #{|x| > tau}, started from "every
+//    candidate active", reaches the root in a few passes over the candidates.
+//  * radix: for |x| >= 0 the IEEE bit pattern is monotone in the value, so a
+//    histogram of the top 11 bits with per-bin counts and integer sums of the
+//    remaining mantissa bits gives phi at every bin edge exactly; the bin that
+//    brackets the root is refined on the next 11 and then 9 bits, after which
+//    a bin holds a single value and the root follows in closed form.  Any
+//    bracket small enough is finished by gathering it and running the window
+//    step on it.
+#pragma once
+
+#include "gsstv_internal.cuh"
+
+namespace gsstv {
+
+// Michelot's fixed point restricted to a window.  One whole block calls it.
+// n_hi, s_hi: count and sum of |x| > theta_hi; cand[0..m_raw): every |x| in
+// (theta_lo, theta_hi].  Returns 0 with *tau_out; 2 when the root lies above
+// the window; 1 when it lies below or the candidates overflowed the buffer.
+static __device__ int l1_window_finish(double n_hi, double s_hi, const float* cand, unsigned m_raw,
+                                       double theta_lo, double theta_hi, double r,
+                                       double* tau_out, double* red_d,
+                                       unsigned long long* red_u) {
+    if (m_raw > kCandCap) return 1;
+    const unsigned m = m_raw;
+    const double phi_hi = s_hi - n_hi * theta_hi - r;
+    if (phi_hi > 0.0) return 2;                        // root above the window
+    Kahan ks;
+    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) ks.add(__ldcg(cand + k));
+    const double sum_c = block_sum(ks.value(), red_d);
+    const double n_all = n_hi + (double)m;
+    const double phi_lo = s_hi + sum_c - n_all * theta_lo - r;
+    if (phi_lo < 0.0) {
+        if (theta_lo <= 0.0) { *tau_out = 0.0; return 0; }  // inside the ball
+        return 1;                                      // root below the window
+    }
+    double tau = (s_hi + sum_c - r) / n_all;
+    unsigned long long prev = m;
+    for (int it = 0; it < 200; ++it) {
+        Kahan ka;
+        unsigned long long c = 0;
+        for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+            const float x = __ldcg(cand + k);
+            if ((double)x > tau) { ka.add(x); ++c; }
+        }
+        const double sa = block_sum(ka.value(), red_d);
+        const unsigned long long ca = block_sum(c, red_u);
+        const double tn = (s_hi + sa - r) / (n_hi + (double)ca);
+        tau = tn;
+        if (ca == prev) break;
+        prev = ca;
+    }
+    *tau_out = tau;
+    return 0;
+}
+
+// Records tau of this iteration and places the window of the next one around
+// the linear extrapolation of the last two thresholds.  The half-width covers
+// twice the last change and is capped so that about kCandTarget candidates
+// are expected (density measured at the last window).  Thread 0 only.
+static __device__ void l1_record_tau(L1Ctl& c, double tau_new, double m_used, double width_used) {
+    c.tau_prev = c.tau;
+    c.have_prev = c.have_tau;
+    c.tau = tau_new;
+    c.have_tau = 1;
+    c.need = NEED_NONE;
+    if (width_used > 0.0 && m_used > 0.0) c.dens = m_used / width_used;
+    if (!(tau_new > 0.0)) {            // ball inactive: window (0, 0]
+        c.theta_lo = 0.f;
+        c.theta_hi = 0.f;
+        c.window_ok = 1;
+        return;
+    }
+    const double d = c.have_prev ? fabs(tau_new - c.tau_prev) : 1e-3 * tau_new;
+    const double center = (c.have_prev && c.tau_prev > 0.0) ? tau_new + (tau_new - c.tau_prev) : tau_new;
+    double hw = 2.0 * d + 1e-7 * tau_new;
+    if (c.dens > 0.0) hw = fmin(hw, 0.5 * kCandTarget / c.dens);
+    const double lo = fmax(center - hw, 0.0);
+    const double hi = center + hw;
+    c.theta_lo = __double2float_rd(lo);
+    c.theta_hi = __double2float_ru(hi);
+    c.window_ok = 1;
+}
+
+// Radix level geometry: bin of a key and its residue (the bits below the bin).
+struct RadixLevel {
+    int level;
+    __device__ __forceinline__ int nbins() const { return level == 2 ? 512 : 2048; }
+    // does the key belong to the bracket fixed by the previous levels?
+    __device__ __forceinline__ bool inside(unsigned key, unsigned prefix) const {
+        return level == 0 ? true : level == 1 ? ((key >> 20) == prefix) : ((key >> 9) == prefix);
+    }
+    __device__ __forceinline__ int bin(unsigned key) const {
+        return level == 0 ? (int)(key >> 20) : level == 1 ? (int)((key >> 9) & 2047u) : (int)(key & 511u);
+    }
+    __device__ __forceinline__ unsigned residue(unsigned key) const {
+        return level == 0 ? (key & 0xfffffu) : level == 1 ? (key & 0x1ffu) : 0u;
+    }
+    __device__ __forceinline__ unsigned lo_key(unsigned prefix, int k) const {
+        return level == 0 ? ((unsigned)k << 20)
+             : level == 1 ? ((prefix << 20) | ((unsigned)k << 9))
+                          : ((prefix << 9) | (unsigned)k);
+    }
+    __device__ __forceinline__ unsigned next_prefix(unsigned prefix, int k) const {
+        return level == 0 ? (unsigned)k : ((prefix << 11) | (unsigned)k);
+    }
+};
+
+// Bracket selection after a radix histogram pass.  One whole block calls it
+// with the merged histogram (hcnt, hres: nbins entries) of one vector.
+// Updates c: either tau is known (NEED_NONE), or the bracket bin is to be
+// gathered (NEED_GATHER), or refined at the next level.
+static __device__ void l1_radix_select(L1Ctl& c, RadixLevel lv, const unsigned long long* hcnt,
+                                       const unsigned long long* hres, double r, double* sh_d,
+                                       unsigned long long* sh_u, int* sh_i) {
+    const int nb = lv.nbins();
+    const int nt = blockDim.x;
+    const int per = (nb + nt - 1) / nt;
+    const int k0 = threadIdx.x * per;
+    const int k1 = min(nb, k0 + per);
+    // 1. chunk totals
+    unsigned long long cnt = 0;
+    double sum = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const unsigned long long ck = __ldcg(hcnt + k);
+        if (ck) {
+            const unsigned key = lv.lo_key(c.prefix, k);
+            sum += (double)ck * key_value(key) + key_ulp(key) * (double)__ldcg(hres + k);
+            cnt += ck;
+        }
+    }
+    // sh_d[0..nt) chunk sums, sh_u[0..nt) chunk counts; suffixes by thread 0
+    sh_d[threadIdx.x] = sum;
+    sh_u[threadIdx.x] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = c.s_above;
+        unsigned long long n = c.n_above;
+        for (int t = nt - 1; t >= 0; --t) {     // exclusive suffix: bins above chunk t
+            const double st = sh_d[t];
+            const unsigned long long nt_ = sh_u[t];
+            sh_d[t] = s;
+            sh_u[t] = n;
+            s += st;
+            n += nt_;
+        }
+    }
+    __syncthreads();
+    // 2. inside the chunk, from the top bin down: phi(lo_k) >= 0 ?
+    double s_run = sh_d[threadIdx.x];
+    unsigned long long n_run = sh_u[threadIdx.x];
+    int best = -1;
+    double best_phi = 0.0, best_s_above = 0.0;
+    unsigned long long best_n_above = 0, best_cnt = 0;
+    for (int k = k1 - 1; k >= k0; --k) {
+        const unsigned long long ck = __ldcg(hcnt + k);
+        const unsigned key = lv.lo_key(c.prefix, k);
+        const double lo = key_value(key);
+        const double sk = ck ? (double)ck * lo + key_ulp(key) * (double)__ldcg(hres + k) : 0.0;
+        const double s_ge = s_run + sk;
+        const unsigned long long n_ge = n_run + ck;
+        const double phi = s_ge - (double)n_ge * lo - r;
+        if (phi >= 0.0) {
+            best = k; best_phi = phi; best_s_above = s_run; best_n_above = n_run; best_cnt = ck;
+            break;
+        }
+        s_run = s_ge;
+        n_run = n_ge;
+    }
+    __syncthreads();
+    // 3. the highest bracket over the block
+    if (threadIdx.x == 0) sh_i[0] = -1;
+    __syncthreads();
+    atomicMax(sh_i, best);
+    __syncthreads();
+    const int kb = sh_i[0];
+    if (best == kb && kb >= 0) {
+        const unsigned key = lv.lo_key(c.prefix, kb);
+        const double lo = key_value(key);
+        if (best_phi == 0.0) {
+            l1_record_tau(c, lo, 0.0, 0.0);
+        } else if (lv.level == 2) {
+            // the bracket bin holds one value, inactive for any tau above it
+            l1_record_tau(c, (best_s_above - r) / (double)best_n_above, 0.0, 0.0);
+        } else if (best_cnt <= (unsigned long long)kCandCap) {
+            c.need = NEED_GATHER;
+            c.g_lo = __uint_as_float(key);
+            c.g_hi = __uint_as_float(lv.lo_key(c.prefix, kb + 1) - 1u);
+            c.n_above = best_n_above;
+            c.s_above = best_s_above;
+        } else {
+            c.need = lv.level == 0 ? NEED_RADIX1 : NEED_RADIX2;
+            c.prefix = lv.next_prefix(c.prefix, kb);
+            c.n_above = best_n_above;
+            c.s_above = best_s_above;
+        }
+    }
+    if (threadIdx.x == 0 && kb < 0) {
+        // phi(lower edge of the whole range) < 0: at level 0 the vector is
+        // inside the ball; deeper, only rounding can get here.
+        const double lo0 = lv.level == 0 ? 0.0 : key_value(lv.lo_key(c.prefix, 0));
+        l1_record_tau(c, lo0, 0.0, 0.0);
+    }
+    __syncthreads();
+}
+
+}  // namespace gsstv

@@ -1,0 +1,600 @@
+// K2 (the light pass of one P-PDS iteration), the exact radix search for the
+// l1 thresholds, state conversion kernels and the standalone l1 projection.
+//
+// K2 finishes Algorithm 1 once the l1 thresholds tau_s, tau_t are known:
+//   s+ = P_{B1,alpha}(s~) = soft(s~, tau_s),  t+ = soft(t~, tau_t),
+//   s' = 2 s+ - s,  t' = 2 t+ - t,
+//   y3+ = y3 + g3 D_v t'                                   (needs row i+1)
+//   y4' = y4 + g4 (u' + s' + t'),  q = y4' - g4 v,
+// and reduces ||q||^2: the l2-ball step of Algorithm 1 (Eq. 23 through
+// Moreau's identity, Eq. 3) is y4+ = (1 - c) q with c = min(1, eps g4 / ||q||),
+// which the next iteration applies when it reads q.  It also reduces the two
+// norms of the stopping rule (Eq. 28).
+#include <algorithm>
+
+#include "gsstv_internal.cuh"
+#include "gsstv_l1.cuh"
+
+namespace gsstv {
+namespace {
+
+constexpr int NT = 256;
+constexpr int K2_ROWS = 8;   // rows per thread strip in K2
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ float4 ld(const float* p) { return *reinterpret_cast<const float4*>(p); }
+    static __device__ __forceinline__ void st(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+};
+template <> struct Vec4<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 ld(const __nv_bfloat16* p) {
+        uint2 r = *reinterpret_cast<const uint2*>(p);
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float4 v) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 r;
+        r.x = *reinterpret_cast<unsigned*>(&a);
+        r.y = *reinterpret_cast<unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = r;
+    }
+};
+template <> struct Vec4<__half> {
+    static __device__ __forceinline__ float4 ld(const __half* p) {
+        uint2 r = *reinterpret_cast<const uint2*>(p);
+        float2 a = __half22float2(*reinterpret_cast<__half2*>(&r.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2*>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ void st(__half* p, float4 v) {
+        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        uint2 r;
+        r.x = *reinterpret_cast<unsigned*>(&a);
+        r.y = *reinterpret_cast<unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = r;
+    }
+};
+__device__ __forceinline__ float comp(const float4& v, int k) {
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set_comp(float4& v, int k, float x) {
+    if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
+}
+
+// ---------------------------------------------------------------------------
+// K2
+// ---------------------------------------------------------------------------
+template <typename T>
+struct K2Args {
+    Geom g;
+    const T *u, *u_n, *s, *t, *y3, *q;
+    const float* v;
+    T *s_n, *t_n, *y3_n, *q_n;
+    IterParams p;
+    Scal* sc;
+    double* part;       // 3 doubles per CTA
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
+    __shared__ double red_d[64];
+    __shared__ int is_last;
+    const Geom g = a.g;
+    const IterParams& P = a.p;
+    const float cs = (float)(1.0 - a.sc->c[P.parity]);
+    const float tau_s = (float)a.sc->ctl[0].tau;
+    const float tau_t = (float)a.sc->ctl[1].tau;
+    const int quads = g.p2 / 4;
+    const int strips = (g.n1 + K2_ROWS - 1) / K2_ROWS;
+    const long long items = (long long)g.n3 * strips * quads;
+    Kahan aq, adu, au;
+    for (long long it = blockIdx.x * (long long)NT + threadIdx.x; it < items; it += (long long)gridDim.x * NT) {
+        const int qd = (int)(it % quads);
+        const long long rest = it / quads;
+        const int strip = (int)(rest % strips);
+        const int b = (int)(rest / strips);
+        const int j = qd * 4;
+        const int i_s = strip * K2_ROWS;
+        const int i_own = min(i_s + K2_ROWS, g.n1);            // own rows [i_s, i_own)
+        const int i_last = min(i_s + K2_ROWS, g.n1 - 1);       // plus one halo row if any
+        float4 y3m = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i_s >= 1) y3m = Vec4<T>::ld(a.y3 + g.at(b, i_s - 1, j));
+        float4 tprev = y3m, y3prev = y3m;
+        for (int i = i_s; i <= i_last; ++i) {
+            const long long o = g.at(b, i, j);
+            const float4 s4 = Vec4<T>::ld(a.s + o), t4 = Vec4<T>::ld(a.t + o);
+            const float4 y34 = Vec4<T>::ld(a.y3 + o), q4 = Vec4<T>::ld(a.q + o);
+            const bool own = i < i_own;
+            float4 u0 = make_float4(0, 0, 0, 0), u1 = u0, v4 = u0;
+            if (own) {
+                u0 = Vec4<T>::ld(a.u + o);
+                u1 = Vec4<T>::ld(a.u_n + o);
+                v4 = *reinterpret_cast<const float4*>(a.v + o);
+            }
+            float4 sp4, tp4, qn4, tb4, y3n4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float y4 = __fmul_rn(cs, comp(q4, k));
+                float xs, xt;
+                s_t_tilde(comp(s4, k), comp(t4, k), comp(y34, k), comp(y3m, k), comp(q4, k), cs, i,
+                          g.n1, P.gamma_s, P.gamma_t, xs, xt);
+                const float sp = soft(xs, tau_s), tp = soft(xt, tau_t);
+                const float sb = 2.f * sp - comp(s4, k), tb = 2.f * tp - comp(t4, k);
+                set_comp(sp4, k, sp);
+                set_comp(tp4, k, tp);
+                set_comp(tb4, k, tb);
+                // y3 of the row above, now that t' of this row is known
+                set_comp(y3n4, k, comp(y3prev, k) + P.gamma_y3 * (tb - comp(tprev, k)));
+                if (own) {
+                    const float uo = comp(u0, k), un = comp(u1, k);
+                    const float ub = 2.f * un - uo;
+                    const float y4p = y4 + P.gamma_y4 * (ub + sb + tb);
+                    const float qn = y4p - P.gamma_y4 * comp(v4, k);
+                    set_comp(qn4, k, qn);
+                    if (j + k < g.n2) {
+                        aq.add(qn * qn);
+                        const float du = un - uo;
+                        adu.add(du * du);
+                        au.add(uo * uo);
+                    }
+                }
+            }
+            if (i > i_s) Vec4<T>::st(a.y3_n + o - g.p2, y3n4);
+            if (own) {
+                Vec4<T>::st(a.s_n + o, sp4);
+                Vec4<T>::st(a.t_n + o, tp4);
+                Vec4<T>::st(a.q_n + o, qn4);
+            }
+            y3m = y34;
+            y3prev = y34;
+            tprev = tb4;
+        }
+        // the last row has D_v t' = 0: y3 is unchanged there
+        if (i_own == g.n1) Vec4<T>::st(a.y3_n + g.at(b, g.n1 - 1, j), y3prev);
+    }
+    const double q2 = block_sum(aq.value(), red_d);
+    const double du2 = block_sum(adu.value(), red_d);
+    const double u2 = block_sum(au.value(), red_d);
+    if (threadIdx.x == 0) {
+        a.part[3 * blockIdx.x] = q2;
+        a.part[3 * blockIdx.x + 1] = du2;
+        a.part[3 * blockIdx.x + 2] = u2;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->k2_ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += NT) {
+        s0 += __ldcg(a.part + 3 * k);
+        s1 += __ldcg(a.part + 3 * k + 1);
+        s2 += __ldcg(a.part + 3 * k + 2);
+    }
+    s0 = block_sum(s0, red_d);
+    s1 = block_sum(s1, red_d);
+    s2 = block_sum(s2, red_d);
+    if (threadIdx.x == 0) {
+        Scal* sc = a.sc;
+        double c = 1.0;
+        if (!isfinite(s0) || !isfinite(s1) || !isfinite(s2)) {
+            sc->error |= 1;
+        } else if (s0 > 0.0) {
+            c = fmin(1.0, P.eps * (double)P.gamma_y4 / sqrt(s0));
+        }
+        sc->c[P.parity ^ 1] = c;
+        sc->q2 = s0;
+        sc->du2 = s1;
+        sc->u2 = s2;
+        sc->iter++;
+        sc->k2_ticket = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// value sources of the radix search: the cube's s~, t~ or a flat vector
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CubeSrc {
+    Geom g;
+    const T *s, *t, *y3, *q;
+    const Scal* sc;
+    int parity;
+    float gs, gt;
+    __device__ long long count() const { return (long long)g.n3 * g.n1 * g.n2; }
+    __device__ float cscale() const { return (float)(1.0 - sc->c[parity]); }
+    // |s~| (v = 0) and |t~| (v = 1) of voxel l
+    __device__ void get(long long l, float cs, float& as, float& at) const {
+        const long long nn = (long long)g.n1 * g.n2;
+        const int b = (int)(l / nn);
+        const long long r = l - b * nn;
+        const int i = (int)(r / g.n2);
+        const int j = (int)(r - (long long)i * g.n2);
+        const long long o = g.at(b, i, j);
+        const float y3u = i >= 1 ? ldT(y3 + o - g.p2) : 0.f;
+        float xs, xt;
+        s_t_tilde(ldT(s + o), ldT(t + o), ldT(y3 + o), y3u, ldT(q + o), cs, i, g.n1, gs, gt, xs, xt);
+        as = fabsf(xs);
+        at = fabsf(xt);
+    }
+};
+
+struct FlatSrc {
+    const float* x;
+    long long n;
+    __device__ long long count() const { return n; }
+    __device__ float cscale() const { return 1.f; }
+    __device__ void get(long long l, float, float& a0, float& a1) const { a0 = fabsf(x[l]); a1 = 0.f; }
+};
+
+struct SearchArgs {
+    Scal* sc;
+    L1Work w;
+    int nvec;        // 2 for the cube (s, t), 1 for a flat vector
+};
+
+// Radix histogram pass of one level for every vector that needs it; the last
+// CTA selects the bracket.
+template <typename Src>
+__global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a, const int level) {
+    extern __shared__ __align__(16) unsigned long long hsm[];   // [2][2048] counts, [2][2048] residues
+    __shared__ double sh_d[NT];
+    __shared__ unsigned long long sh_u[NT];
+    __shared__ int sh_i[1];
+    __shared__ int is_last;
+    const int want = NEED_RADIX0 + level;
+    bool need[2];
+    need[0] = a.sc->ctl[0].need == want;
+    need[1] = a.nvec > 1 && a.sc->ctl[1].need == want;
+    if (!need[0] && !need[1]) return;
+    const RadixLevel lv{level};
+    const int nb = lv.nbins();
+    unsigned long long* hc = hsm;
+    unsigned long long* hr = hsm + 2 * kHistBins;
+    for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) { hc[k] = 0; hr[k] = 0; }
+    __syncthreads();
+    const unsigned pre0 = a.sc->ctl[0].prefix, pre1 = a.sc->ctl[1].prefix;
+    const long long n = src.count();
+    const float cs = src.cscale();
+    for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < n; l += (long long)gridDim.x * NT) {
+        float x0, x1;
+        src.get(l, cs, x0, x1);
+        if (need[0]) {
+            const unsigned key = __float_as_uint(x0);
+            if (lv.inside(key, pre0)) {
+                const int bn = lv.bin(key);
+                atomicAdd(hc + bn, 1ull);
+                const unsigned rs = lv.residue(key);
+                if (rs) atomicAdd(hr + bn, (unsigned long long)rs);
+            }
+        }
+        if (need[1]) {
+            const unsigned key = __float_as_uint(x1);
+            if (lv.inside(key, pre1)) {
+                const int bn = lv.bin(key);
+                atomicAdd(hc + kHistBins + bn, 1ull);
+                const unsigned rs = lv.residue(key);
+                if (rs) atomicAdd(hr + kHistBins + bn, (unsigned long long)rs);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) {
+        if ((k % kHistBins) >= nb) continue;
+        if (hc[k]) atomicAdd(a.w.hcnt + k, hc[k]);
+        if (hr[k]) atomicAdd(a.w.hres + k, hr[k]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->fb_ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int v = 0; v < 2; ++v) {
+        if (!need[v]) continue;
+        l1_radix_select(a.sc->ctl[v], lv, a.w.hcnt + v * kHistBins, a.w.hres + v * kHistBins,
+                        a.sc->radius[v], sh_d, sh_u, sh_i);
+    }
+    for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) { a.w.hcnt[k] = 0; a.w.hres[k] = 0; }
+    if (threadIdx.x == 0) a.sc->fb_ticket = 0;
+}
+
+// Gathers the bracket bin of every vector that needs it and finishes tau.
+template <typename Src>
+__global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a) {
+    __shared__ double red_d[64];
+    __shared__ unsigned long long red_u[64];
+    __shared__ int is_last;
+    bool need[2];
+    need[0] = a.sc->ctl[0].need == NEED_GATHER;
+    need[1] = a.nvec > 1 && a.sc->ctl[1].need == NEED_GATHER;
+    if (!need[0] && !need[1]) return;
+    const float lo0 = a.sc->ctl[0].g_lo, hi0 = a.sc->ctl[0].g_hi;
+    const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
+    const long long n = src.count();
+    const float cs = src.cscale();
+    for (long long base = blockIdx.x * (long long)NT; base < n; base += (long long)gridDim.x * NT) {
+        const long long l = base + threadIdx.x;
+        float x0 = 0.f, x1 = 0.f;
+        const bool valid = l < n;
+        if (valid) src.get(l, cs, x0, x1);
+        if (need[0]) append_candidate(valid && x0 > lo0 && x0 <= hi0, x0, a.w.cand[0], &a.sc->acc[0].m);
+        if (need[1]) append_candidate(valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->g_ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int v = 0; v < 2; ++v) {
+        if (!need[v]) continue;
+        L1Ctl& C = a.sc->ctl[v];
+        const double r = a.sc->radius[v];
+        const unsigned m = __ldcg(&a.sc->acc[v].m);
+        const double glo = C.g_lo, ghi = C.g_hi;
+        const double na = (double)C.n_above, sa = C.s_above;
+        double tau = 0.0;
+        const int rc = l1_window_finish(na, sa, a.w.cand[v], m, glo, ghi, r, &tau, red_d, red_u);
+        if (threadIdx.x == 0) {
+            if (rc == 2 && na > 0.0) {
+                // the root lies between the largest value of the bin and the
+                // next bin's edge: every value of the bin is inactive
+                tau = (sa - r) / na;
+            } else if (rc != 0) {
+                a.sc->error |= 2;
+            }
+            l1_record_tau(C, tau, (double)min(m, kCandCap), ghi - glo);
+            a.sc->acc[v].m = 0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.sc->g_ticket = 0;
+}
+
+// out = soft(x, tau) for the standalone projection
+__global__ void k_apply_flat(const float* x, float* out, long long n, const Scal* sc) {
+    const double tau = sc->ctl[0].tau;
+    const float tf = (float)tau;
+    for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < n; l += (long long)gridDim.x * NT)
+        out[l] = tau > 0.0 ? soft(x[l], tf) : x[l];
+}
+
+// ---------------------------------------------------------------------------
+// layout conversion: (ncubes, n3, n1, *) arrays between pitches and types
+// ---------------------------------------------------------------------------
+template <typename S, typename D>
+__global__ void k_convert(const S* src, long long src_pitch, long long src_cube, D* dst,
+                          long long dst_pitch, long long dst_cube, int n1, int n2, int n3,
+                          int ncubes, const double* scale) {
+    const float f = scale ? (float)(1.0 - *scale) : 1.f;
+    const long long per = (long long)n3 * n1 * n2;
+    const long long total = per * ncubes;
+    for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < total; l += (long long)gridDim.x * NT) {
+        const int cb = (int)(l / per);
+        const long long r = l - cb * per;
+        const long long row = r / n2;             // b * n1 + i
+        const int j = (int)(r - row * n2);
+        const float x = ldT(src + cb * src_cube + row * src_pitch + j);
+        stT(dst + cb * dst_cube + row * dst_pitch + j, scale ? f * x : x);
+    }
+}
+
+int grid_for(long long n) {
+    long long b = (n + NT - 1) / NT;
+    return (int)std::max(1ll, std::min(b, 152ll * 16));
+}
+
+template <typename T>
+int launch_k2_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc, double* part,
+                int part_cap, cudaStream_t st) {
+    K2Args<T> a;
+    a.g = g;
+    a.u = (const T*)b.u; a.u_n = (const T*)b.u_n; a.s = (const T*)b.s; a.t = (const T*)b.t;
+    a.y3 = (const T*)b.y3; a.q = (const T*)b.q; a.v = b.v;
+    a.s_n = (T*)b.s_n; a.t_n = (T*)b.t_n; a.y3_n = (T*)b.y3_n; a.q_n = (T*)b.q_n;
+    a.p = p;
+    a.sc = sc;
+    a.part = part;
+    const int ctas = std::min(k2_grid_ctas(g), part_cap);
+    k2_light<T><<<ctas, NT, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+template <typename Src>
+int launch_radix_src(const Src& src, long long n, const SearchArgs& a, int level, cudaStream_t st) {
+    const size_t smem = 4 * kHistBins * sizeof(unsigned long long);
+    k_radix<Src><<<std::min(grid_for(n), 152 * 2), NT, smem, st>>>(src, a, level);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+template <typename T>
+CubeSrc<T> make_cube_src(const Geom& g, const IterBufs& b, const IterParams& p, const Scal* sc) {
+    CubeSrc<T> c;
+    c.g = g;
+    c.s = (const T*)b.s; c.t = (const T*)b.t; c.y3 = (const T*)b.y3; c.q = (const T*)b.q;
+    c.sc = sc;
+    c.parity = p.parity;
+    c.gs = p.gamma_s;
+    c.gt = p.gamma_t;
+    return c;
+}
+
+template <typename T>
+int launch_fallback_t(int level, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
+                      const L1Work& w, cudaStream_t st) {
+    SearchArgs a{sc, w, 2};
+    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc);
+    return launch_radix_src(src, (long long)g.n3 * g.n1 * g.n2, a, level, st);
+}
+
+template <typename T>
+int launch_gather_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc, const L1Work& w,
+                    cudaStream_t st) {
+    SearchArgs a{sc, w, 2};
+    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc);
+    const long long n = (long long)g.n3 * g.n1 * g.n2;
+    k_gather<CubeSrc<T>><<<std::min(grid_for(n), 152 * 4), NT, 0, st>>>(src, a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+template <typename S, typename D>
+int launch_convert(const S* src, long long sp, long long sc_, D* dst, long long dp, long long dc,
+                   const Geom& g, int ncubes, const double* scale, cudaStream_t st) {
+    const long long n = (long long)g.n3 * g.n1 * g.n2 * ncubes;
+    k_convert<S, D><<<grid_for(n), NT, 0, st>>>(src, sp, sc_, dst, dp, dc, g.n1, g.n2, g.n3, ncubes, scale);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace
+
+int light_configure(int storage) {
+    const int smem = 4 * kHistBins * sizeof(unsigned long long);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (storage) {
+        case 0: e = cudaFuncSetAttribute(k_radix<CubeSrc<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+        case 1: e = cudaFuncSetAttribute(k_radix<CubeSrc<__nv_bfloat16>>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+        case 2: e = cudaFuncSetAttribute(k_radix<CubeSrc<__half>>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    }
+    if (e != cudaSuccess) return -3;
+    e = cudaFuncSetAttribute(k_radix<FlatSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e == cudaSuccess ? 0 : -3;
+}
+
+int k2_grid_ctas(const Geom& g) {
+    const long long items = (long long)g.n3 * ((g.n1 + K2_ROWS - 1) / K2_ROWS) * (g.p2 / 4);
+    return grid_for(items);
+}
+
+int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
+              double* part, int part_cap, cudaStream_t st) {
+    switch (storage) {
+        case 0: return launch_k2_t<float>(g, b, p, sc, part, part_cap, st);
+        case 1: return launch_k2_t<__nv_bfloat16>(g, b, p, sc, part, part_cap, st);
+        case 2: return launch_k2_t<__half>(g, b, p, sc, part, part_cap, st);
+    }
+    return -1;
+}
+
+
+int launch_fallback(int storage, int level, const Geom& g, const IterBufs& b, const IterParams& p,
+                    Scal* sc, const L1Work& w, cudaStream_t st) {
+    switch (storage) {
+        case 0: return launch_fallback_t<float>(level, g, b, p, sc, w, st);
+        case 1: return launch_fallback_t<__nv_bfloat16>(level, g, b, p, sc, w, st);
+        case 2: return launch_fallback_t<__half>(level, g, b, p, sc, w, st);
+    }
+    return -1;
+}
+
+int launch_gather(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
+                  const L1Work& w, cudaStream_t st) {
+    switch (storage) {
+        case 0: return launch_gather_t<float>(g, b, p, sc, w, st);
+        case 1: return launch_gather_t<__nv_bfloat16>(g, b, p, sc, w, st);
+        case 2: return launch_gather_t<__half>(g, b, p, sc, w, st);
+    }
+    return -1;
+}
+
+// dense float32 (ncubes, n3, n1, n2)  ->  pitched storage cubes
+int launch_pack(int storage, const float* src, void* dst, const Geom& g, int ncubes, cudaStream_t st) {
+    const long long sp = g.n2, scb = (long long)g.n3 * g.n1 * g.n2;
+    switch (storage) {
+        case 0: return launch_convert(src, sp, scb, (float*)dst, g.p2, g.cube, g, ncubes, nullptr, st);
+        case 1: return launch_convert(src, sp, scb, (__nv_bfloat16*)dst, g.p2, g.cube, g, ncubes, nullptr, st);
+        case 2: return launch_convert(src, sp, scb, (__half*)dst, g.p2, g.cube, g, ncubes, nullptr, st);
+    }
+    return -1;
+}
+
+// pitched float32 (the handle's v)  ->  pitched storage cube
+int launch_pitched_to_storage(int storage, const float* src, void* dst, const Geom& g, cudaStream_t st) {
+    switch (storage) {
+        case 0: return launch_convert(src, g.p2, g.cube, (float*)dst, g.p2, g.cube, g, 1, nullptr, st);
+        case 1: return launch_convert(src, g.p2, g.cube, (__nv_bfloat16*)dst, g.p2, g.cube, g, 1, nullptr, st);
+        case 2: return launch_convert(src, g.p2, g.cube, (__half*)dst, g.p2, g.cube, g, 1, nullptr, st);
+    }
+    return -1;
+}
+
+// dense float32 (n3, n1, n2)  ->  pitched float32
+int launch_dense_to_pitched(const float* src, float* dst, const Geom& g, cudaStream_t st) {
+    return launch_convert(src, (long long)g.n2, (long long)g.n3 * g.n1 * g.n2, dst, g.p2, g.cube, g, 1,
+                          nullptr, st);
+}
+
+int launch_unpack(int storage, const void* src, float* dst, const Geom& g, int ncubes, cudaStream_t st) {
+    const long long dp = g.n2, dcb = (long long)g.n3 * g.n1 * g.n2;
+    switch (storage) {
+        case 0: return launch_convert((const float*)src, g.p2, g.cube, dst, dp, dcb, g, ncubes, nullptr, st);
+        case 1: return launch_convert((const __nv_bfloat16*)src, g.p2, g.cube, dst, dp, dcb, g, ncubes, nullptr, st);
+        case 2: return launch_convert((const __half*)src, g.p2, g.cube, dst, dp, dcb, g, ncubes, nullptr, st);
+    }
+    return -1;
+}
+
+int launch_scale_unpack(int storage, const void* q, const double* c, float* dst, const Geom& g,
+                        cudaStream_t st) {
+    const long long dp = g.n2, dcb = (long long)g.n3 * g.n1 * g.n2;
+    switch (storage) {
+        case 0: return launch_convert((const float*)q, g.p2, g.cube, dst, dp, dcb, g, 1, c, st);
+        case 1: return launch_convert((const __nv_bfloat16*)q, g.p2, g.cube, dst, dp, dcb, g, 1, c, st);
+        case 2: return launch_convert((const __half*)q, g.p2, g.cube, dst, dp, dcb, g, 1, c, st);
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// standalone projection of a flat device vector onto an l1 ball
+// ---------------------------------------------------------------------------
+int l1_project_standalone(const float* x, long long n, double radius, float* out, double* tau,
+                          cudaStream_t st) {
+    if (light_configure(0) != 0) return -3;
+    Scal* sc = nullptr;
+    L1Work w{};
+    size_t bytes_hist = 2 * kHistBins * sizeof(unsigned long long);
+    int rc = 0;
+    if (cudaMalloc(&sc, sizeof(Scal)) != cudaSuccess) return -2;
+    if (cudaMalloc(&w.hcnt, bytes_hist) != cudaSuccess || cudaMalloc(&w.hres, bytes_hist) != cudaSuccess ||
+        cudaMalloc(&w.cand[0], kCandCap * sizeof(float)) != cudaSuccess) {
+        rc = -2;
+    }
+    if (rc == 0) {
+        w.cand[1] = w.cand[0];
+        Scal h{};
+        h.radius[0] = radius;
+        h.ctl[0].need = radius > 0.0 ? NEED_RADIX0 : NEED_NONE;
+        h.ctl[0].tau = radius > 0.0 ? 0.0 : (double)INFINITY;
+        if (cudaMemcpyAsync(sc, &h, sizeof(Scal), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemsetAsync(w.hcnt, 0, bytes_hist, st) != cudaSuccess ||
+            cudaMemsetAsync(w.hres, 0, bytes_hist, st) != cudaSuccess)
+            rc = -3;
+        const FlatSrc src{x, n};
+        const SearchArgs a{sc, w, 1};
+        for (int level = 0; level < 3 && rc == 0; ++level) rc = launch_radix_src(src, n, a, level, st);
+        if (rc == 0) {
+            k_gather<FlatSrc><<<std::min(grid_for(n), 152 * 4), NT, 0, st>>>(src, a);
+            k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
+            if (cudaGetLastError() != cudaSuccess) rc = -3;
+        }
+        if (rc == 0) {
+            if (cudaMemcpyAsync(&h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                rc = -3;
+            else if (h.error) rc = -6;
+            else if (tau) *tau = h.ctl[0].tau;
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(sc);
+    cudaFree(w.hcnt);
+    cudaFree(w.hres);
+    cudaFree(w.cand[0]);
+    return rc;
+}
+
+}  // namespace gsstv

@@ -1,0 +1,144 @@
+"""PyTorch-facing wrapper of the C ABI: device memory and streams from torch,
+every computation in libgsstv.
+
+Cubes are float32 tensors of shape (N3, N1, N2) -- band, row (vertical),
+column (horizontal) -- contiguous, the layout of include/gsstv.h.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+STORAGE = {"fp32": B.GSSTV_FP32, "bf16": B.GSSTV_BF16, "fp16": B.GSSTV_FP16}
+STATE_KEYS = ("u", "s", "t", "w1", "w2", "y1", "y2", "y3", "y4")
+STATE_LEAD = {"u": (), "s": (), "t": (), "w1": (3, 2), "w2": (3, 2), "y1": (2,), "y2": (2,),
+              "y3": (), "y4": ()}
+
+
+def make_params(**kw) -> B.GsstvParams:
+    """gsstv_default_params() with fields overridden by keyword; ``storage``
+    may be given as "fp32" / "bf16" / "fp16"."""
+    p = B.gsstv_default_params()
+    for k, v in kw.items():
+        if k == "storage" and isinstance(v, str):
+            v = STORAGE[v]
+        if k == "tau_mode" and isinstance(v, str):
+            v = {"auto": B.GSSTV_TAU_AUTO, "exact": B.GSSTV_TAU_EXACT}[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class GeoSSTVSolver:
+    """One libgsstv handle for N1 x N2 x N3 cubes on the current CUDA device."""
+
+    def __init__(self, n1: int, n2: int, n3: int, params: B.GsstvParams | None = None,
+                 stream: torch.cuda.Stream | None = None, **kw):
+        if not torch.cuda.is_available():
+            raise RuntimeError("GeoSSTVSolver needs a CUDA device")
+        B.load()
+        self.shape = (n3, n1, n2)
+        self.params = params if params is not None else make_params(**kw)
+        self.stream = stream or torch.cuda.current_stream()
+        self.h = B.gsstv_create(n1, n2, n3, self.params, self.stream.cuda_stream)
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            B.gsstv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers ---------------------------------------------------------------
+    def _dev(self, x: torch.Tensor, lead=()) -> torch.Tensor:
+        want = tuple(lead) + self.shape
+        if tuple(x.shape) != want:
+            raise ValueError(f"expected shape {want}, got {tuple(x.shape)}")
+        if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("expected a contiguous float32 CUDA tensor")
+        return x
+
+    def _empty(self, lead=()):
+        return torch.empty(tuple(lead) + self.shape, dtype=torch.float32, device="cuda")
+
+    # -- API -------------------------------------------------------------------
+    def set_params(self, params: B.GsstvParams | None = None, **kw):
+        if params is None:
+            params = self.params
+            for k, v in kw.items():
+                setattr(params, k, STORAGE.get(v, v) if k == "storage" else v)
+        B.gsstv_set_params(self.h, params)
+        self.params = params
+
+    def solve(self, v: torch.Tensor):
+        """Runs max_iter passes from the standard start; returns (u, s, t, iters)."""
+        self._dev(v)
+        u, s, t = self._empty(), self._empty(), self._empty()
+        n = B.gsstv_solve(self.h, v.data_ptr(), u.data_ptr(), s.data_ptr(), t.data_ptr())
+        return u, s, t, n
+
+    def solve_host(self, v_host: torch.Tensor, u_host: torch.Tensor, s_host=None, t_host=None) -> int:
+        """End to end from host memory (pinned tensors give the fastest copies)."""
+        for x in (v_host, u_host, s_host, t_host):
+            if x is not None and (x.is_cuda or x.dtype != torch.float32 or tuple(x.shape) != self.shape
+                                  or not x.is_contiguous()):
+                raise ValueError("expected contiguous float32 host tensors of the cube shape")
+        return B.gsstv_solve_host(self.h, v_host.data_ptr(), u_host.data_ptr(),
+                                  s_host.data_ptr() if s_host is not None else None,
+                                  t_host.data_ptr() if t_host is not None else None)
+
+    def load(self, v: torch.Tensor, reset: bool = True):
+        B.gsstv_load_observation(self.h, self._dev(v).data_ptr())
+        if reset:
+            B.gsstv_reset_state(self.h)
+
+    def reset(self):
+        B.gsstv_reset_state(self.h)
+
+    def iterate(self, n: int) -> int:
+        return B.gsstv_iterate(self.h, n)
+
+    def get_state(self) -> dict:
+        st = {k: self._empty(STATE_LEAD[k]) for k in STATE_KEYS}
+        B.gsstv_get_state(self.h, {k: v.data_ptr() for k, v in st.items()})
+        return st
+
+    def set_state(self, st: dict):
+        tens = {k: self._dev(st[k], STATE_LEAD[k]) for k in STATE_KEYS}
+        B.gsstv_set_state(self.h, {k: v.data_ptr() for k, v in tens.items()})
+
+    def stats(self) -> dict:
+        s = B.gsstv_get_stats(self.h)
+        return {k: getattr(s, k) for k, _ in B.GsstvStats._fields_}
+
+    def reset_stats(self):
+        B.gsstv_reset_stats(self.h)
+
+    def set_timing(self, on: bool):
+        B.gsstv_set_timing(self.h, on)
+
+    def device_bytes(self) -> int:
+        return B.gsstv_device_bytes(self.h)
+
+
+def project_l1ball(x: torch.Tensor, radius: float, out: torch.Tensor | None = None):
+    """Projection of a float32 CUDA vector onto the l1 ball; returns (out, tau)."""
+    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    out = torch.empty_like(x) if out is None else out
+    tau = B.gsstv_project_l1ball(x.data_ptr(), x.numel(), float(radius), out.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    return out, tau
