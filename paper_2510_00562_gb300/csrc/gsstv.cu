@@ -25,6 +25,7 @@ struct gsstv_handle {
     Geom g{};
     gsstv_params p{};
     cudaStream_t st = nullptr;
+    cudaStream_t cap = nullptr;   // private stream used only to capture graphs
     int esz = 4;
     void *u[2]{}, *s[2]{}, *t[2]{}, *y3[2]{}, *q[2]{};
     void *w1[2]{}, *w2[2]{}, *y1[2]{}, *y2[2]{};
@@ -87,9 +88,10 @@ int dalloc(gsstv_handle* h, void** out, size_t bytes) {
 void free_all(gsstv_handle* h) {
     for (int k = 0; k < 2; ++k)
         if (h->gexec[k]) { cudaGraphExecDestroy(h->gexec[k]); h->gexec[k] = nullptr; }
-    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev) if (e) cudaEventDestroy(e);
     h->ev.clear();
-    if (h->st) cudaStreamSynchronize(h->st);
+    cudaStreamSynchronize(h->st);
+    if (h->cap) { cudaStreamDestroy(h->cap); h->cap = nullptr; }
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
 }
@@ -129,37 +131,40 @@ IterParams iparams(const gsstv_handle* h, int par) {
 
 int map_launch(int rc) { return rc == 0 ? GSSTV_OK : rc == -1 ? GSSTV_ERR_ARG : GSSTV_ERR_CUDA; }
 
-// One iteration from parity `par` (reads buffers par, writes par ^ 1).
-int enqueue_iteration(gsstv_handle* h, int par, bool timed) {
+// One iteration from parity `par` (reads buffers par, writes par ^ 1) on `st`.
+int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
     const IterBufs b = bufs(h, par);
     const IterParams ip = iparams(h, par);
     const int sto = h->p.storage;
     if (timed) {
         if (h->ev_used + 2 > (int)h->ev.size()) return GSSTV_ERR_INTERNAL;
-        TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used], h->st)));
+        TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used], st)));
     }
-    TRY(map_launch(launch_k1(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, h->st)));
+    TRY(map_launch(launch_k1(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, st)));
     if (timed) {
-        TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used + 1], h->st)));
+        TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used + 1], st)));
         h->ev_used += 2;
     }
     for (int level = 0; level < 3; ++level)
-        TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, h->st)));
-    TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, h->st)));
-    TRY(map_launch(launch_k2(sto, h->g, b, ip, h->sc, h->k2_part, h->k2_cap, h->st)));
+        TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, st)));
+    TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, st)));
+    TRY(map_launch(launch_k2(sto, h->g, b, ip, h->sc, h->k2_part, h->k2_cap, st)));
     return GSSTV_OK;
 }
 
+// Captures `len` iterations starting at parity `par` on the private capture
+// stream (the caller's stream may be the legacy default stream, which cannot
+// be captured); the executable graph is launched on the caller's stream.
 int build_graph(gsstv_handle* h, int par, int len) {
     cudaGraph_t graph = nullptr;
-    TRY(cuda_rc(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal)));
+    TRY(cuda_rc(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal)));
     int rc = GSSTV_OK;
     int p = par;
     for (int k = 0; k < len && rc == GSSTV_OK; ++k) {
-        rc = enqueue_iteration(h, p, false);
+        rc = enqueue_iteration(h, p, false, h->cap);
         p ^= 1;
     }
-    cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
     if (rc != GSSTV_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
     if (e != cudaSuccess) return GSSTV_ERR_CUDA;
     e = cudaGraphInstantiate(&h->gexec[par], graph, 0);
@@ -193,7 +198,7 @@ int run_block(gsstv_handle* h, int n) {
             h->stats.iterations += G;
         } else {
             if (h->timing && h->ev_used + 2 > (int)h->ev.size()) TRY(flush_timing(h));
-            TRY(enqueue_iteration(h, h->parity, h->timing != 0));
+            TRY(enqueue_iteration(h, h->parity, h->timing != 0, h->st));
             h->parity ^= 1;
             --n;
             h->stats.iterations += 1;
@@ -269,6 +274,10 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
         if (rc == GSSTV_OK) rc = dalloc(h, &h->y1[k], 2 * cb);
         if (rc == GSSTV_OK) rc = dalloc(h, &h->y2[k], 2 * cb);
     }
+    if (rc == GSSTV_OK && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        h->cap = nullptr;
+        rc = GSSTV_ERR_CUDA;
+    }
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->v, (size_t)h->g.cube * sizeof(float));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->sc, sizeof(Scal));
     if (rc == GSSTV_OK && (k1_configure(p->storage) != 0 || light_configure(p->storage) != 0)) rc = GSSTV_ERR_CUDA;
@@ -288,8 +297,6 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
     }
     if (rc == GSSTV_OK) rc = upload_scalars(h, initial_scalars(h->p));
     if (rc != GSSTV_OK) {
-        for (auto& e : h->ev) if (e) cudaEventDestroy(e);
-        h->ev.clear();
         free_all(h);
         delete h;
         return rc;
