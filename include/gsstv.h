@@ -166,6 +166,31 @@ int64_t gsstv_device_bytes(const gsstv_handle* h);
 int gsstv_project_l1ball(const float* d_x, int64_t n, double radius,
                          float* d_out, double* tau_out, void* stream);
 
+/* Allocation-free variant of gsstv_project_l1ball.  The paper has no
+ * counterpart: it exists for callers that must not allocate device memory --
+ * code whose device memory belongs to another allocator (for example a
+ * framework's caching allocator that has already reserved the free memory, so
+ * a raw cudaMalloc may fail or fragment it), latency-critical loops that
+ * cannot afford the device-wide synchronisation of cudaFree, and plugin code
+ * that is not permitted to allocate.
+ *
+ * Same arguments, result and error codes as gsstv_project_l1ball; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch is one
+ * static device array of about 1.1 MB (a controller block, two radix
+ * histograms and a buffer of GSSTV_NOALLOC_MAX_N floats) that every device
+ * loading this library holds until the process exits.
+ *  - n > GSSTV_NOALLOC_MAX_N returns GSSTV_ERR_ARG.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) and configures the kernels, with that device
+ *    current; make that first call before any stream capture.
+ *  - Every call shares the one array (each call clears what must start at
+ *    zero): calls whose GPU work overlaps -- on different streams or from
+ *    different host threads -- race and give wrong results.
+ *  - Synchronises the stream before returning. */
+#define GSSTV_NOALLOC_MAX_N 262144
+int gsstv_project_l1ball_noalloc(const float* d_x, int64_t n, double radius,
+                                 float* d_out, double* tau_out, void* stream);
+
 /* Human-readable text of a return code. */
 const char* gsstv_strerror(int code);
 

@@ -75,8 +75,13 @@ _SIGS = {
     "gsstv_device_bytes": (c_int64, [c_void_p]),
     "gsstv_project_l1ball": (c_int, [c_void_p, c_int64, c_double, c_void_p,
                                      ctypes.POINTER(c_double), c_void_p]),
+    "gsstv_project_l1ball_noalloc": (c_int, [c_void_p, c_int64, c_double, c_void_p,
+                                             ctypes.POINTER(c_double), c_void_p]),
     "gsstv_strerror": (ctypes.c_char_p, [c_int]),
 }
+
+# largest n accepted by gsstv_project_l1ball_noalloc (include/gsstv.h)
+GSSTV_NOALLOC_MAX_N = 262144
 
 EXPORTED = tuple(_SIGS)
 
@@ -198,6 +203,17 @@ def gsstv_project_l1ball(d_x: int, n: int, radius: float, d_out: int, stream: in
     tau = c_double(0.0)
     _check(load().gsstv_project_l1ball(d_x, n, radius, d_out, ctypes.byref(tau), stream or None),
            "gsstv_project_l1ball")
+    return tau.value
+
+
+def gsstv_project_l1ball_noalloc(d_x: int, n: int, radius: float, d_out: int,
+                                 stream: int | None = None) -> float:
+    """Same as gsstv_project_l1ball, for callers that may not allocate device
+    memory: the scratch is a static device array, n <= GSSTV_NOALLOC_MAX_N, and
+    calls whose GPU work overlaps race on that array."""
+    tau = c_double(0.0)
+    _check(load().gsstv_project_l1ball_noalloc(d_x, n, radius, d_out, ctypes.byref(tau), stream or None),
+           "gsstv_project_l1ball_noalloc")
     return tau.value
 
 

@@ -598,3 +598,104 @@ int l1_project_standalone(const float* x, long long n, double radius, float* out
 }
 
 }  // namespace gsstv
+
+// ---------------------------------------------------------------------------
+// Allocation-free l1-ball projection.
+//
+// Same kernels as gsstv_project_l1ball, but every scratch byte (controller
+// block, radix histograms, candidate buffer) lives in one file-scope device
+// array instead of cudaMalloc'd memory, for callers that are not allowed to
+// allocate device memory.  The candidate buffer here holds
+// GSSTV_NOALLOC_MAX_N values; a radix bracket never holds more values than
+// the whole input, so every n <= GSSTV_NOALLOC_MAX_N fits, and larger n are
+// refused.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#include "gsstv.h"
+
+namespace gsstv {
+namespace {
+
+constexpr size_t kNaScal = (sizeof(Scal) + 255) / 256 * 256;
+constexpr size_t kNaHist = 2 * kHistBins * sizeof(unsigned long long);
+constexpr size_t kNaCand = (size_t)GSSTV_NOALLOC_MAX_N * sizeof(float);
+constexpr size_t kNaBytes = kNaScal + 2 * kNaHist + kNaCand;
+
+// The scratch array: on every device that loads this library, until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kMaxDevices = 64;
+unsigned char* g_na_ptr[kMaxDevices] = {};     // device address of the array, per device
+std::mutex g_na_mutex;
+
+__global__ void k_noalloc_init(Scal* sc, double radius) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Scal z;
+        memset(&z, 0, sizeof(z));
+        z.radius[0] = radius;
+        z.ctl[0].need = radius > 0.0 ? NEED_RADIX0 : NEED_NONE;
+        z.ctl[0].tau = radius > 0.0 ? 0.0 : (double)__int_as_float(0x7f800000);
+        *sc = z;
+    }
+}
+
+// Resolves the array's device address on the current device (first call on
+// that device only) and configures the kernels it launches.
+int noalloc_setup(unsigned char** base) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -3;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return -3;
+        if (light_configure(0) != 0) return -3;
+        g_na_ptr[dev] = (unsigned char*)p;
+    }
+    *base = g_na_ptr[dev];
+    return 0;
+}
+
+}  // namespace
+
+int l1_project_noalloc(const float* x, long long n, double radius, float* out, double* tau,
+                       cudaStream_t st) {
+    unsigned char* base = nullptr;
+    if (noalloc_setup(&base) != 0) return -3;
+    Scal* sc = reinterpret_cast<Scal*>(base);
+    L1Work w{};
+    w.hcnt = reinterpret_cast<unsigned long long*>(base + kNaScal);
+    w.hres = reinterpret_cast<unsigned long long*>(base + kNaScal + kNaHist);
+    w.cand[0] = w.cand[1] = reinterpret_cast<float*>(base + kNaScal + 2 * kNaHist);
+    // the previous call's contents stay in the array: clear what must start at zero
+    k_noalloc_init<<<1, 32, 0, st>>>(sc, radius);
+    if (cudaGetLastError() != cudaSuccess) return -3;
+    if (cudaMemsetAsync(w.hcnt, 0, 2 * kNaHist, st) != cudaSuccess) return -3;
+    const FlatSrc src{x, n};
+    const SearchArgs a{sc, w, 1};
+    for (int level = 0; level < 3; ++level)
+        if (launch_radix_src(src, n, a, level, st) != 0) return -3;
+    k_gather<FlatSrc><<<std::min(grid_for(n), 152 * 4), NT, 0, st>>>(src, a);
+    k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
+    if (cudaGetLastError() != cudaSuccess) return -3;
+    double t = 0.0;
+    int err = 0;
+    if (cudaMemcpyAsync(&t, &sc->ctl[0].tau, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&err, &sc->error, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return -3;
+    if (err) return -6;
+    if (tau) *tau = t;
+    return 0;
+}
+
+}  // namespace gsstv
+
+extern "C" int gsstv_project_l1ball_noalloc(const float* d_x, int64_t n, double radius, float* d_out,
+                                            double* tau_out, void* stream) {
+    if (!d_x || !d_out || n < 0 || !(radius >= 0.0) || !std::isfinite(radius)) return GSSTV_ERR_ARG;
+    if (n > GSSTV_NOALLOC_MAX_N) return GSSTV_ERR_ARG;
+    if (n == 0) { if (tau_out) *tau_out = 0.0; return GSSTV_OK; }
+    const int rc = gsstv::l1_project_noalloc(d_x, (long long)n, radius, d_out, tau_out, (cudaStream_t)stream);
+    return rc == 0 ? GSSTV_OK : rc == -6 ? GSSTV_ERR_INTERNAL : GSSTV_ERR_CUDA;
+}
