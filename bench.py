@@ -61,22 +61,31 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def k1_traffic_record(storage):
-    """ncu dram bytes of one K1 launch, if recorded for the current source."""
+K1_SOURCE = {"tma": "k_stencil_tma.cu", "coop": "k_stencil.cu"}
+K1_KERNEL = {"tma": "k1_tma (fused stencil pass, TMA-fed)", "coop": "k1_stencil (fused stencil pass)"}
+
+
+def k1_variant():
+    return "coop" if os.environ.get("GSSTV_K1") == "coop" else "tma"
+
+
+def k1_traffic_record(storage, variant):
+    """ncu dram bytes per voxel of one K1 launch, if recorded for the current source."""
     path = os.path.join(ROOT, "profiles", "k1_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return None
-    from paper_2510_00562_gb300 import build
     import hashlib
-    src = open(os.path.join(build.CSRC, "k_stencil.cu"), "rb").read()
-    if rec.get("k_stencil_sha256") != hashlib.sha256(src).hexdigest():
-        return None
-    ent = rec.get(storage)
+    from paper_2510_00562_gb300 import build
+    ent = rec.get(variant)
     if not ent:
         return None
-    return float(ent["bytes_per_voxel"])
+    src = open(os.path.join(build.CSRC, K1_SOURCE[variant]), "rb").read()
+    if ent.get("sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    st = ent.get(storage)
+    return float(st["bytes_per_voxel"]) if st else None
 
 
 class ClockSampler:
@@ -158,6 +167,12 @@ def max_over_ranks(x, dist):
 def barrier(dist):
     if dist is not None:
         dist.barrier()
+
+
+def job_throughput(world, nvox, steps, ms_max):
+    """Whole-job voxel-iterations per second: every rank ran `steps` passes over
+    its own cube of `nvox` voxels, and the job took the slowest rank's time."""
+    return world * nvox * steps / (ms_max * 1e-3)
 
 
 # ---------------------------------------------------------------------------
@@ -272,7 +287,11 @@ def run_gpu(args):
     st = sol.stats()
     sol.set_timing(False)
     ms_max = max_over_ranks(ms, dist)
-    value = world * nvox * args.steps / (ms_max * 1e-3)
+    value = job_throughput(world, nvox, args.steps, ms_max)
+
+    pf = None
+    if not args.no_precision_form and args.storage == "fp32" and world == 1:
+        pf = precision_form(sol, pb, args)
 
     # end to end through the public host API: copies in, solve, copies out
     sol.set_params(make_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03,
@@ -296,7 +315,8 @@ def run_gpu(args):
     k1_ms = st["k1_ms"] / max(st["k1_launches"], 1)
     k1_bytes = K1_WORDS * esz * nvox
     achieved = k1_bytes / (k1_ms * 1e-3) / 1e9
-    traffic_bpv = k1_traffic_record(args.storage)
+    variant = k1_variant()
+    traffic_bpv = k1_traffic_record(args.storage, variant)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -308,7 +328,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (no flush): state "
                          f"{ITER_WORDS * esz * nvox / 1e9:.1f} GB moved per step"},
-        "roofline": {"bound": "hbm", "kernel": "k1_stencil (fused stencil pass)",
+        "roofline": {"bound": "hbm", "kernel": K1_KERNEL[variant],
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": traffic_bpv * nvox if traffic_bpv else None,
@@ -324,6 +344,8 @@ def run_gpu(args):
                         "state reset, iterations, D2H of u, s, t"},
         "gpu_launches": 6 * args.steps,
     }
+    if pf:
+        line["precision_form"] = pf
     clk_s = clk.summary()
     if clk_s:
         line["clocks"] = clk_s
@@ -338,6 +360,57 @@ def run_gpu(args):
     return 0
 
 
+def precision_form(sol32, pb, args):
+    """Mixed storage vs FP32 on the same cube and iteration budget N: FP32 for N
+    passes, against BF16 iterates (FP32 arithmetic) for 0.8 N passes followed
+    by an FP32 phase of 0.2 N passes warm-started from the 16-bit state.
+    Returns the 16-bit phase throughput and the MPSNR of both results against
+    the clean cube."""
+    import torch
+    from paper_2510_00562_gb300 import metrics
+    from paper_2510_00562_gb300.solver import GeoSSTVSolver, make_params
+    n1, n2, n3 = args.shape
+    nvox = n1 * n2 * n3
+    N = args.pf_iters
+    n16 = (N * 4) // 5
+    kw = dict(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03, graph_iters=16)
+    v = torch.from_numpy(pb["v"]).cuda()
+    stream = torch.cuda.current_stream()
+    sol32.set_params(make_params(max_iter=N, **kw))
+    u32 = sol32.solve(v)[0]
+    m32 = metrics.mpsnr(u32.cpu().numpy(), pb["u_bar"])
+    del u32
+    out = {"iterations": N, "fp32_mpsnr_db": m32}
+    for storage in ("bf16", "fp16"):
+        with GeoSSTVSolver(n1, n2, n3, make_params(max_iter=n16, storage=storage, **kw), stream=stream) as lo:
+            lo.load(v)
+            lo.iterate(8)                        # graphs built, caches warm
+            lo.reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lo.iterate(n16)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = lo.get_state()
+        m16 = metrics.mpsnr(st["u"].cpu().numpy(), pb["u_bar"])
+        sol32.set_params(make_params(max_iter=N - n16, **kw))
+        sol32.load(v, reset=False)
+        sol32.set_state(st)
+        del st
+        sol32.iterate(N - n16)
+        uf = sol32.get_state()["u"]
+        mf = metrics.mpsnr(uf.cpu().numpy(), pb["u_bar"])
+        del uf
+        out[storage] = {"passes_16bit": n16, "passes_fp32": N - n16,
+                        "value_16bit_phase": nvox * n16 / (ms * 1e-3), "unit": UNIT,
+                        "mpsnr_after_16bit_db": m16, "mpsnr_db": mf, "delta_vs_fp32_db": mf - m32}
+    sol32.set_params(make_params(max_iter=args.steps, **kw))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,6 +420,9 @@ def main(argv=None):
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-form", action="store_true")
+    ap.add_argument("--pf-iters", type=int, default=500,
+                    help="iteration budget of the mixed-vs-FP32 comparison")
     ap.add_argument("--shape", default="512x512x224",
                     help="N1xN2xN3; anything but the default is a profiling case, not a bench line")
     args = ap.parse_args(argv)

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -37,6 +38,8 @@ struct gsstv_handle {
     int k2_cap = 0;
     int k1_ctas = 0;
     int parity = 0;               // ping-pong index that holds the current state
+    int k1_variant = 1;           // 1: TMA-fed K1, 0: cooperative-load K1 (GSSTV_K1=coop)
+    K1Maps maps[2];               // tensor maps of the buffers read at parity 0 / 1
     cudaGraphExec_t gexec[2]{};
     int graph_len = 0;
     int timing = 0;
@@ -140,7 +143,10 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
         if (h->ev_used + 2 > (int)h->ev.size()) return GSSTV_ERR_INTERNAL;
         TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used], st)));
     }
-    TRY(map_launch(launch_k1(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, st)));
+    if (h->k1_variant == 1)
+        TRY(map_launch(launch_k1_tma(sto, h->g, h->maps[par], b, ip, h->sc, h->l1, st)));
+    else
+        TRY(map_launch(launch_k1(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, st)));
     if (timed) {
         TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used + 1], st)));
         h->ev_used += 2;
@@ -214,6 +220,7 @@ int read_scalars(gsstv_handle* h, Scal* out) {
 
 int error_of(const Scal& s) {
     if (s.error & 1) return GSSTV_ERR_NONFINITE;
+    if (s.error & 4) return GSSTV_ERR_TIMEOUT;
     if (s.error) return GSSTV_ERR_INTERNAL;
     return GSSTV_OK;
 }
@@ -280,8 +287,14 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
     }
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->v, (size_t)h->g.cube * sizeof(float));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->sc, sizeof(Scal));
-    if (rc == GSSTV_OK && (k1_configure(p->storage) != 0 || light_configure(p->storage) != 0)) rc = GSSTV_ERR_CUDA;
-    h->k1_ctas = k1_grid_ctas(h->g);
+    if (rc == GSSTV_OK && (k1_configure(p->storage) != 0 || light_configure(p->storage) != 0 ||
+                           k1_tma_configure(p->storage) != 0))
+        rc = GSSTV_ERR_CUDA;
+    {
+        const char* ev = std::getenv("GSSTV_K1");   // debugging aid: pick the K1 variant
+        h->k1_variant = (ev && std::strcmp(ev, "coop") == 0) ? 0 : 1;
+    }
+    h->k1_ctas = std::max(k1_grid_ctas(h->g), k1_tma_ctas(h->g));
     h->k2_cap = k2_grid_ctas(h->g);
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.cand[0], kCandCap * sizeof(float));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.cand[1], kCandCap * sizeof(float));
@@ -294,6 +307,10 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
         h->ev.resize(512);
         for (auto& e : h->ev)
             if (rc == GSSTV_OK && cudaEventCreate(&e) != cudaSuccess) { e = nullptr; rc = GSSTV_ERR_CUDA; }
+    }
+    for (int par = 0; par < 2 && rc == GSSTV_OK; ++par) {
+        const IterBufs b = bufs(h, par);
+        if (k1_tma_maps(p->storage, h->g, b, &h->maps[par]) != 0) rc = GSSTV_ERR_CUDA;
     }
     if (rc == GSSTV_OK) rc = upload_scalars(h, initial_scalars(h->p));
     if (rc != GSSTV_OK) {

@@ -13,6 +13,7 @@
 // the scale is applied when y4 is next read instead of in an extra pass.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -91,7 +92,7 @@ struct Scal {
     L1Acc acc[2];
     double radius[2];          // alpha, beta
     unsigned int k1_ticket, k2_ticket, fb_ticket, g_ticket;
-    int error;                 // bit 0: non-finite norm; bit 1: internal
+    int error;                 // bit 0: non-finite norm; bit 1: internal; bit 2: a bounded wait timed out
     int pad0;
     double q2, du2, u2;        // norms of the last K2 pass
     long long iter;
@@ -99,7 +100,8 @@ struct Scal {
 
 constexpr int kHistBins = 2048;        // radix histogram bins per vector
 constexpr unsigned kCandCap = 1u << 20; // candidate capacity per vector
-constexpr double kCandTarget = 8192.0;  // window sized for about this many candidates
+constexpr double kCandTarget = 65536.0; // window sized for about this many candidates
+constexpr unsigned kGatherMax = 1u << 16; // a radix bracket this small is gathered, a larger one refined
 
 // Device workspace of the l1 machinery (shared layout with the standalone
 // projection entry point).
@@ -221,6 +223,17 @@ struct IterParams {
     int parity;                  // iteration parity (selects c[])
     int tau_exact;               // 1: skip the window statistics
 };
+
+// Tensor maps over the current-parity buffers read by the TMA-fed K1.
+struct K1Maps {
+    CUtensorMap y1, y2, w1, w2, u, q, s, t, y3;
+};
+
+int k1_tma_ctas(const Geom& g);
+int k1_tma_configure(int storage);
+int k1_tma_maps(int storage, const Geom& g, const IterBufs& b, K1Maps* m);
+int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p,
+                  Scal* sc, const L1Work& w, cudaStream_t st);
 
 int launch_k1(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
               const L1Work& w, int n_cta_slots, cudaStream_t st);

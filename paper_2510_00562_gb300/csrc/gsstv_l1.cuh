@@ -192,7 +192,7 @@ static __device__ void l1_radix_select(L1Ctl& c, RadixLevel lv, const unsigned l
         } else if (lv.level == 2) {
             // the bracket bin holds one value, inactive for any tau above it
             l1_record_tau(c, (best_s_above - r) / (double)best_n_above, 0.0, 0.0);
-        } else if (best_cnt <= (unsigned long long)kCandCap) {
+        } else if (best_cnt <= (unsigned long long)kGatherMax) {
             c.need = NEED_GATHER;
             c.g_lo = __uint_as_float(key);
             c.g_hi = __uint_as_float(lv.lo_key(c.prefix, kb + 1) - 1u);

@@ -204,30 +204,54 @@ struct CubeSrc {
     const Scal* sc;
     int parity;
     float gs, gt;
-    __device__ long long count() const { return (long long)g.n3 * g.n1 * g.n2; }
-    __device__ float cscale() const { return (float)(1.0 - sc->c[parity]); }
-    // |s~| (v = 0) and |t~| (v = 1) of voxel l
-    __device__ void get(long long l, float cs, float& as, float& at) const {
-        const long long nn = (long long)g.n1 * g.n2;
-        const int b = (int)(l / nn);
-        const long long r = l - b * nn;
-        const int i = (int)(r / g.n2);
-        const int j = (int)(r - (long long)i * g.n2);
-        const long long o = g.at(b, i, j);
-        const float y3u = i >= 1 ? ldT(y3 + o - g.p2) : 0.f;
-        float xs, xt;
-        s_t_tilde(ldT(s + o), ldT(t + o), ldT(y3 + o), y3u, ldT(q + o), cs, i, g.n1, gs, gt, xs, xt);
-        as = fabsf(xs);
-        at = fabsf(xt);
+    // Calls f(valid, |s~|, |t~|) for every voxel this thread owns, four
+    // columns at a time in row order; every lane of a warp makes the same
+    // number of calls (warp-collective work inside f is allowed).
+    template <typename F>
+    __device__ void visit(F&& f) const {
+        const float cs = (float)(1.0 - sc->c[parity]);
+        const unsigned quads = (unsigned)g.p2 / 4u;
+        const unsigned n1 = (unsigned)g.n1;
+        const unsigned total = (unsigned)g.n3 * n1 * quads;     // < 2^31 for any cube that fits
+        for (unsigned base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+            const unsigned item = base + threadIdx.x;
+            const bool live = item < total;
+            const unsigned row = live ? item / quads : 0u;       // b * n1 + i
+            const int j = (int)(item - row * quads) * 4;
+            const int i = (int)(row % n1);
+            float4 s4 = make_float4(0, 0, 0, 0), t4 = s4, y34 = s4, yu4 = s4, q4 = s4;
+            if (live) {
+                const long long o = (long long)row * g.p2 + j;
+                s4 = Vec4<T>::ld(s + o);
+                t4 = Vec4<T>::ld(t + o);
+                y34 = Vec4<T>::ld(y3 + o);
+                q4 = Vec4<T>::ld(q + o);
+                if (i >= 1) yu4 = Vec4<T>::ld(y3 + o - g.p2);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float xs = 0.f, xt = 0.f;
+                const bool valid = live && j + k < g.n2;
+                if (valid)
+                    s_t_tilde(comp(s4, k), comp(t4, k), comp(y34, k), comp(yu4, k), comp(q4, k), cs, i, g.n1,
+                              gs, gt, xs, xt);
+                f(valid, fabsf(xs), fabsf(xt));
+            }
+        }
     }
 };
 
 struct FlatSrc {
     const float* x;
     long long n;
-    __device__ long long count() const { return n; }
-    __device__ float cscale() const { return 1.f; }
-    __device__ void get(long long l, float, float& a0, float& a1) const { a0 = fabsf(x[l]); a1 = 0.f; }
+    template <typename F>
+    __device__ void visit(F&& f) const {
+        for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+            const long long l = base + threadIdx.x;
+            const bool valid = l < n;
+            f(valid, valid ? fabsf(x[l]) : 0.f, 0.f);
+        }
+    }
 };
 
 struct SearchArgs {
@@ -257,30 +281,29 @@ __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a,
     for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) { hc[k] = 0; hr[k] = 0; }
     __syncthreads();
     const unsigned pre0 = a.sc->ctl[0].prefix, pre1 = a.sc->ctl[1].prefix;
-    const long long n = src.count();
-    const float cs = src.cscale();
-    for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < n; l += (long long)gridDim.x * NT) {
-        float x0, x1;
-        src.get(l, cs, x0, x1);
+    const int lane = threadIdx.x & 31;
+    // lanes that fall in the same bin add their count and residues once
+    auto insert = [&](int v, bool take, unsigned key) {
+        const unsigned bn = take ? (unsigned)lv.bin(key) : 0xffffffffu;
+        const unsigned grp = __match_any_sync(0xffffffffu, bn);
+        if (take) {
+            const unsigned tot = __reduce_add_sync(grp, lv.residue(key));
+            if (lane == __ffs(grp) - 1) {
+                atomicAdd(hc + v * kHistBins + bn, (unsigned long long)__popc(grp));
+                if (tot) atomicAdd(hr + v * kHistBins + bn, (unsigned long long)tot);
+            }
+        }
+    };
+    src.visit([&](bool valid, float x0, float x1) {
         if (need[0]) {
             const unsigned key = __float_as_uint(x0);
-            if (lv.inside(key, pre0)) {
-                const int bn = lv.bin(key);
-                atomicAdd(hc + bn, 1ull);
-                const unsigned rs = lv.residue(key);
-                if (rs) atomicAdd(hr + bn, (unsigned long long)rs);
-            }
+            insert(0, valid && lv.inside(key, pre0), key);
         }
         if (need[1]) {
             const unsigned key = __float_as_uint(x1);
-            if (lv.inside(key, pre1)) {
-                const int bn = lv.bin(key);
-                atomicAdd(hc + kHistBins + bn, 1ull);
-                const unsigned rs = lv.residue(key);
-                if (rs) atomicAdd(hr + kHistBins + bn, (unsigned long long)rs);
-            }
+            insert(1, valid && lv.inside(key, pre1), key);
         }
-    }
+    });
     __syncthreads();
     for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) {
         if ((k % kHistBins) >= nb) continue;
@@ -314,16 +337,10 @@ __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a
     if (!need[0] && !need[1]) return;
     const float lo0 = a.sc->ctl[0].g_lo, hi0 = a.sc->ctl[0].g_hi;
     const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
-    const long long n = src.count();
-    const float cs = src.cscale();
-    for (long long base = blockIdx.x * (long long)NT; base < n; base += (long long)gridDim.x * NT) {
-        const long long l = base + threadIdx.x;
-        float x0 = 0.f, x1 = 0.f;
-        const bool valid = l < n;
-        if (valid) src.get(l, cs, x0, x1);
+    src.visit([&](bool valid, float x0, float x1) {
         if (need[0]) append_candidate(valid && x0 > lo0 && x0 <= hi0, x0, a.w.cand[0], &a.sc->acc[0].m);
         if (need[1]) append_candidate(valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
-    }
+    });
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->g_ticket, 1u) == gridDim.x - 1);
@@ -407,7 +424,7 @@ int launch_k2_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
 template <typename Src>
 int launch_radix_src(const Src& src, long long n, const SearchArgs& a, int level, cudaStream_t st) {
     const size_t smem = 4 * kHistBins * sizeof(unsigned long long);
-    k_radix<Src><<<std::min(grid_for(n), 152 * 2), NT, smem, st>>>(src, a, level);
+    k_radix<Src><<<std::min(grid_for(n), 152 * 3), NT, smem, st>>>(src, a, level);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

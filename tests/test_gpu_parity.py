@@ -113,9 +113,16 @@ def _random_problem(n1, n2, n3, seed):
                        beta=0.4 * np.abs(t64).sum(), omega=0.05)
 
 
+@pytest.fixture(params=["tma", "coop"])
+def k1_variant(request, monkeypatch):
+    """Both implementations of the fused stencil kernel (read at handle creation)."""
+    monkeypatch.setenv("GSSTV_K1", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("tau_mode", ["auto", "exact"])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_one_pass_matches_oracle(shape, tau_mode):
+def test_one_pass_matches_oracle(shape, tau_mode, k1_variant):
     n1, n2, n3 = shape
     rs, v, kw = _random_problem(n1, n2, n3, seed=n1 * 7 + n3)
     p = make_params(tau_mode=tau_mode, graph_iters=0, **kw)
@@ -154,10 +161,12 @@ def _solve_both(n1, n2, n3, iters, tau_mode="auto", graph_iters=16, omega=0.03):
 
 
 @pytest.mark.parametrize("tau_mode", ["auto", "exact"])
-def test_solve_parity_small(tau_mode):
+def test_solve_parity_small(tau_mode, k1_variant):
     pb, (u, s, t), st, stats = _solve_both(40, 36, 12, 300, tau_mode=tau_mode)
-    for name, a, b in (("u", u, st.u), ("s", s, st.s), ("t", t, st.t)):
-        assert rel(a, b) < 1e-5, (name, rel(a, b))
+    errs = {name: rel(a, b) for name, a, b in (("u", u, st.u), ("s", s, st.s), ("t", t, st.t))}
+    print(f"\nparity 40x36x12 300 it {tau_mode} {k1_variant}: {errs}")
+    for name, e in errs.items():
+        assert e < 1e-5, (name, e)
     d = abs(metrics.mpsnr(u, pb["u_bar"]) - metrics.mpsnr(st.u, pb["u_bar"]))
     assert d <= 0.01
     if tau_mode == "exact":
@@ -169,9 +178,11 @@ def test_solve_parity_64x64x32_2000_iterations():
     pepper, stripes on 5% of the columns, 2000 iterations."""
     pb, (u, s, t), st, stats = _solve_both(64, 64, 32, 2000)
     errs = {name: rel(a, b) for name, a, b in (("u", u, st.u), ("s", s, st.s), ("t", t, st.t))}
-    assert max(errs.values()) < 1e-5, errs
     m_gpu = metrics.mpsnr(u, pb["u_bar"])
     m_ref = metrics.mpsnr(st.u, pb["u_bar"])
+    print(f"\nparity 64x64x32 2000 it: {errs} mpsnr gpu {m_gpu:.4f} oracle {m_ref:.4f} "
+          f"window hits {stats['tau_window_hits']} exact runs {stats['tau_exact_runs']}")
+    assert max(errs.values()) < 1e-5, errs
     assert abs(m_gpu - m_ref) <= 0.01, (m_gpu, m_ref)
     assert m_gpu > metrics.mpsnr(pb["v"], pb["u_bar"]) + 3.0     # it denoises
 
