@@ -342,7 +342,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 3 * 4 * nvox / args.steps,
                 "note": "one gsstv_solve_host call of `steps` iterations: pinned H2D of v, "
                         "state reset, iterations, D2H of u, s, t"},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,
     }
     if pf:
         line["precision_form"] = pf

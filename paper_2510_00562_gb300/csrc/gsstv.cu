@@ -1,7 +1,8 @@
 // Host driver and C ABI of libgsstv (declared in include/gsstv.h).
 //
-// One iteration of Algorithm 1 is five launches on the handle's stream:
+// One iteration of Algorithm 1 is seven launches on the handle's stream:
 //   K1  fused stencil pass (u, w1, w2, y1, y2 and the l1 window statistics);
+//   W   one retry window for a threshold whose K1 window missed;
 //   R0, R1, R2  radix passes of the exact l1-threshold search (each returns at
 //       once unless the previous step left that level pending);
 //   G   gather of the bracket bin (same early return);
@@ -151,6 +152,7 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
         TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used + 1], st)));
         h->ev_used += 2;
     }
+    TRY(map_launch(launch_window(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, st)));
     for (int level = 0; level < 3; ++level)
         TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, st)));
     TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, st)));

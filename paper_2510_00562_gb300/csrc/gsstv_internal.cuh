@@ -19,6 +19,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace gsstv {
 
 // ---------------------------------------------------------------------------
@@ -41,6 +43,58 @@ template <typename T> __device__ __forceinline__ float ldT(const T* p) { return 
 template <typename T> __device__ __forceinline__ void stT(T* p, float x) { Store<T>::st(p, x); }
 
 // ---------------------------------------------------------------------------
+// Stochastic rounding of the 16-bit iterate stores.  With round-to-nearest, a
+// 16-bit iterate stops moving once the per-iteration increment of Algorithm 1
+// falls below half its last place; rounding up with probability equal to the
+// discarded fraction keeps every store unbiased, so small increments still
+// accumulate on average.  Random bits: a counter-based stream per voxel and
+// iteration -- Wellons' "lowbias32" integer mixer seeds it, a 32-bit LCG
+// (Numerical Recipes constants) steps it, and each store takes the high bits.
+// The float32 path draws nothing.
+// ---------------------------------------------------------------------------
+struct SRStream {
+    unsigned r;
+    __device__ __forceinline__ SRStream(unsigned idx, unsigned iter, unsigned var) {
+        unsigned x = idx ^ (iter * 0x9E3779B9u) ^ (var * 0x85EBCA6Bu);
+        x ^= x >> 16; x *= 0x7feb352du;
+        x ^= x >> 15; x *= 0x846ca68bu;
+        x ^= x >> 16;
+        r = x;
+    }
+    __device__ __forceinline__ unsigned next() { r = r * 1664525u + 1013904223u; return r; }
+};
+
+template <typename T> struct StoreSR {
+    static __device__ __forceinline__ void st(T* p, float x, SRStream&) { stT(p, x); }
+};
+template <> struct StoreSR<__nv_bfloat16> {
+    // bf16 keeps the top 16 bits of the float32 pattern: add 16 random bits
+    // below the cut, then truncate (sign-magnitude, so this rounds |x| up with
+    // the probability of the discarded fraction)
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float x, SRStream& sr) {
+        unsigned u = __float_as_uint(x);
+        if ((u & 0x7f800000u) != 0x7f800000u) u += sr.next() >> 16;
+        const unsigned short h = (unsigned short)(u >> 16);
+        *reinterpret_cast<unsigned short*>(p) = h;
+    }
+};
+template <> struct StoreSR<__half> {
+    // fp16 normals keep 10 of the 23 mantissa bits: add 13 random bits below
+    // the cut and convert toward zero; tiny values (fp16 subnormals) round to
+    // nearest
+    static __device__ __forceinline__ void st(__half* p, float x, SRStream& sr) {
+        const unsigned u = __float_as_uint(x);
+        const unsigned e = u & 0x7f800000u;
+        if (e >= 0x38800000u && e != 0x7f800000u)       // |x| >= 2^-14
+            *p = __float2half_rz(__uint_as_float(u + (sr.next() >> 19)));
+        else
+            *p = __float2half_rn(x);
+    }
+};
+template <typename T> __device__ __forceinline__ void stS(T* p, float x, SRStream& sr) { StoreSR<T>::st(p, x, sr); }
+template <typename T> constexpr bool kIs16 = !std::is_same<T, float>::value;
+
+// ---------------------------------------------------------------------------
 // geometry
 // ---------------------------------------------------------------------------
 struct Geom {
@@ -61,6 +115,7 @@ enum L1Need : int {
     NEED_RADIX1 = 2,    // level 1 (bits 19..9) inside the level-0 bin
     NEED_RADIX2 = 3,    // level 2 (bits 8..0): single-value bins
     NEED_GATHER = 4,    // gather the bracket bin and finish with Michelot steps
+    NEED_WINDOW = 5,    // one more windowed pass (after a missed window), then radix
 };
 
 struct L1Ctl {
@@ -91,7 +146,7 @@ struct Scal {
     L1Ctl ctl[2];
     L1Acc acc[2];
     double radius[2];          // alpha, beta
-    unsigned int k1_ticket, k2_ticket, fb_ticket, g_ticket;
+    unsigned int k1_ticket, k2_ticket, fb_ticket, g_ticket, w_ticket, pad1;
     int error;                 // bit 0: non-finite norm; bit 1: internal; bit 2: a bounded wait timed out
     int pad0;
     double q2, du2, u2;        // norms of the last K2 pass
@@ -244,6 +299,8 @@ int launch_fallback(int storage, int level, const Geom& g, const IterBufs& b, co
                     Scal* sc, const L1Work& w, cudaStream_t st);
 int launch_gather(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
                   const L1Work& w, cudaStream_t st);
+int launch_window(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
+                  const L1Work& w, int part_cap, cudaStream_t st);
 int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
               double* part, int part_cap, cudaStream_t st);
 int k2_grid_ctas(const Geom& g);

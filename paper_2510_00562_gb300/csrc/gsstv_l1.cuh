@@ -23,6 +23,13 @@
 
 namespace gsstv {
 
+// What a window pass learned besides tau (for placing a retry window).
+struct WinInfo {
+    double phi_hi = 0.0;   // phi at the top of the window
+    double phi_lo = 0.0;   // phi at the bottom (valid when the candidates fit)
+    double n_lo = 0.0;     // count of |x| > theta_lo
+};
+
 // Michelot's fixed point restricted to a window.  One whole block calls it.
 // n_hi, s_hi: count and sum of |x| > theta_hi; cand[0..m_raw): every |x| in
 // (theta_lo, theta_hi].  Returns 0 with *tau_out; 2 when the root lies above
@@ -30,16 +37,18 @@ namespace gsstv {
 static __device__ int l1_window_finish(double n_hi, double s_hi, const float* cand, unsigned m_raw,
                                        double theta_lo, double theta_hi, double r,
                                        double* tau_out, double* red_d,
-                                       unsigned long long* red_u) {
+                                       unsigned long long* red_u, WinInfo* info = nullptr) {
+    const double phi_hi = s_hi - n_hi * theta_hi - r;
+    if (info) info->phi_hi = phi_hi;
     if (m_raw > kCandCap) return 1;
     const unsigned m = m_raw;
-    const double phi_hi = s_hi - n_hi * theta_hi - r;
     if (phi_hi > 0.0) return 2;                        // root above the window
     Kahan ks;
     for (unsigned k = threadIdx.x; k < m; k += blockDim.x) ks.add(__ldcg(cand + k));
     const double sum_c = block_sum(ks.value(), red_d);
     const double n_all = n_hi + (double)m;
     const double phi_lo = s_hi + sum_c - n_all * theta_lo - r;
+    if (info) { info->phi_lo = phi_lo; info->n_lo = n_all; }
     if (phi_lo < 0.0) {
         if (theta_lo <= 0.0) { *tau_out = 0.0; return 0; }  // inside the ball
         return 1;                                      // root below the window
@@ -62,6 +71,39 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
     }
     *tau_out = tau;
     return 0;
+}
+
+// After a missed window: place one retry window from the bounds the miss
+// gives, or fall back to the radix search.  phi is convex, non-increasing,
+// with slope -#{|x| > tau}, so
+//   root above (phi(hi) > 0):  tau >= hi + phi(hi) / n_hi          (lower bound)
+//   root below (phi(lo) < 0):  tau <= lo + phi(lo) / n(lo)         (upper bound)
+// The retry window extends from the bound away from the old window by twice
+// the distance, capped near kCandTarget expected candidates.  Thread 0 only.
+static __device__ void l1_after_miss(L1Ctl& c, int rc, const WinInfo& wi, double n_hi, unsigned m,
+                                     double lo, double hi) {
+    double a = -1.0, b = -1.0;
+    if (rc == 2 && n_hi > 0.0) {
+        const double lb = hi + wi.phi_hi / n_hi;
+        double w = fmax(2.0 * (lb - hi), 1e-6 * lb);
+        if (c.dens > 0.0) w = fmin(w, kCandTarget / c.dens);
+        a = lb;
+        b = lb + w;
+    } else if (rc == 1 && m <= kCandCap && wi.n_lo > 0.0 && lo > 0.0) {
+        const double ub = lo + wi.phi_lo / wi.n_lo;
+        double w = fmax(2.0 * (lo - ub), 1e-6 * lo);
+        if (c.dens > 0.0) w = fmin(w, kCandTarget / c.dens);
+        a = fmax(ub - w, 0.0);
+        b = ub;
+    }
+    c.prefix = 0; c.n_above = 0; c.s_above = 0.0; c.exact_runs++;
+    if (b > a && a >= 0.0) {
+        c.need = NEED_WINDOW;
+        c.g_lo = __double2float_rd(a);
+        c.g_hi = __double2float_ru(b);
+    } else {
+        c.need = NEED_RADIX0;
+    }
 }
 
 // Records tau of this iteration and places the window of the next one around

@@ -56,6 +56,16 @@ template <> struct Vec4<__half> {
         *reinterpret_cast<uint2*>(p) = r;
     }
 };
+// four stores of a quad, stochastically rounded for 16-bit storage
+template <typename T>
+__device__ __forceinline__ void st4S(T* p, const float4& v, SRStream& sr) {
+    if constexpr (std::is_same<T, float>::value) {
+        *reinterpret_cast<float4*>(p) = v;
+    } else {
+        stS(p, v.x, sr); stS(p + 1, v.y, sr); stS(p + 2, v.z, sr); stS(p + 3, v.w, sr);
+    }
+}
+
 __device__ __forceinline__ float comp(const float4& v, int k) {
     return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
 }
@@ -86,6 +96,7 @@ __global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
     const float cs = (float)(1.0 - a.sc->c[P.parity]);
     const float tau_s = (float)a.sc->ctl[0].tau;
     const float tau_t = (float)a.sc->ctl[1].tau;
+    const unsigned it32 = (unsigned)a.sc->iter;       // seeds the 16-bit rounding streams
     const int quads = g.p2 / 4;
     const int strips = (g.n1 + K2_ROWS - 1) / K2_ROWS;
     const long long items = (long long)g.n3 * strips * quads;
@@ -141,18 +152,22 @@ __global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
                     }
                 }
             }
-            if (i > i_s) Vec4<T>::st(a.y3_n + o - g.p2, y3n4);
+            SRStream sr((unsigned)o, it32, 5u);
+            if (i > i_s) st4S(a.y3_n + o - g.p2, y3n4, sr);
             if (own) {
-                Vec4<T>::st(a.s_n + o, sp4);
-                Vec4<T>::st(a.t_n + o, tp4);
-                Vec4<T>::st(a.q_n + o, qn4);
+                st4S(a.s_n + o, sp4, sr);
+                st4S(a.t_n + o, tp4, sr);
+                st4S(a.q_n + o, qn4, sr);
             }
             y3m = y34;
             y3prev = y34;
             tprev = tb4;
         }
         // the last row has D_v t' = 0: y3 is unchanged there
-        if (i_own == g.n1) Vec4<T>::st(a.y3_n + g.at(b, g.n1 - 1, j), y3prev);
+        if (i_own == g.n1) {
+            SRStream sr((unsigned)g.at(b, g.n1 - 1, j), it32, 6u);
+            st4S(a.y3_n + g.at(b, g.n1 - 1, j), y3prev, sr);
+        }
     }
     const double q2 = block_sum(aq.value(), red_d);
     const double du2 = block_sum(adu.value(), red_d);
@@ -372,6 +387,75 @@ __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a
     if (threadIdx.x == 0) a.sc->g_ticket = 0;
 }
 
+// One windowed pass after K1's window missed: count and sum of |x| above the
+// retry window, its values as candidates, then Michelot's finish; a second
+// miss leaves the threshold to the radix passes.  Per-CTA partial sums go to
+// pn / ps (the stencil pass's partial arrays, free by now).
+template <typename Src>
+__global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a, unsigned long long* pn,
+                                               double* ps) {
+    __shared__ double red_d[64];
+    __shared__ unsigned long long red_u[64];
+    __shared__ int is_last;
+    bool need[2];
+    need[0] = a.sc->ctl[0].need == NEED_WINDOW;
+    need[1] = a.nvec > 1 && a.sc->ctl[1].need == NEED_WINDOW;
+    if (!need[0] && !need[1]) return;
+    const float lo0 = a.sc->ctl[0].g_lo, hi0 = a.sc->ctl[0].g_hi;
+    const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
+    WinAcc w0, w1;
+    src.visit([&](bool valid, float x0, float x1) {
+        if (need[0]) {
+            const bool hi = valid && x0 > hi0;
+            if (hi) { w0.n++; w0.s.add(x0); }
+            append_candidate(valid && !hi && x0 > lo0, x0, a.w.cand[0], &a.sc->acc[0].m);
+        }
+        if (need[1]) {
+            const bool hi = valid && x1 > hi1;
+            if (hi) { w1.n++; w1.s.add(x1); }
+            append_candidate(valid && !hi && x1 > lo1, x1, a.w.cand[1], &a.sc->acc[1].m);
+        }
+    });
+    const unsigned long long n0 = block_sum(w0.n, red_u), n1 = block_sum(w1.n, red_u);
+    const double s0 = block_sum(w0.s.value(), red_d), s1 = block_sum(w1.s.value(), red_d);
+    if (threadIdx.x == 0) {
+        pn[2 * blockIdx.x] = n0; pn[2 * blockIdx.x + 1] = n1;
+        ps[2 * blockIdx.x] = s0; ps[2 * blockIdx.x + 1] = s1;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->w_ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int v = 0; v < 2; ++v) {
+        if (!need[v]) continue;
+        L1Ctl& C = a.sc->ctl[v];
+        unsigned long long n = 0;
+        double sm = 0.0;
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += NT) {
+            n += __ldcg(pn + 2 * k + v);
+            sm += __ldcg(ps + 2 * k + v);
+        }
+        n = block_sum(n, red_u);
+        sm = block_sum(sm, red_d);
+        const unsigned m = __ldcg(&a.sc->acc[v].m);
+        const double lo = C.g_lo, hi = C.g_hi;
+        double tau = 0.0;
+        const int rc = l1_window_finish((double)n, sm, a.w.cand[v], m, lo, hi, a.sc->radius[v], &tau, red_d, red_u);
+        if (threadIdx.x == 0) {
+            if (rc == 0) {
+                l1_record_tau(C, tau, (double)min(m, kCandCap), hi - lo);
+            } else {
+                C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0;
+            }
+            a.sc->acc[v].m = 0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.sc->w_ticket = 0;
+}
+
 // out = soft(x, tau) for the standalone projection
 __global__ void k_apply_flat(const float* x, float* out, long long n, const Scal* sc) {
     const double tau = sc->ctl[0].tau;
@@ -458,6 +542,17 @@ int launch_gather_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal*
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+template <typename T>
+int launch_window_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc, const L1Work& w,
+                    int part_cap, cudaStream_t st) {
+    SearchArgs a{sc, w, 2};
+    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc);
+    const long long n = (long long)g.n3 * g.n1 * g.n2;
+    const int grid = std::max(1, std::min({grid_for(n), 152 * 4, part_cap}));
+    k_window<CubeSrc<T>><<<grid, NT, 0, st>>>(src, a, w.k1_n, w.k1_s);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 template <typename S, typename D>
 int launch_convert(const S* src, long long sp, long long sc_, D* dst, long long dp, long long dc,
                    const Geom& g, int ncubes, const double* scale, cudaStream_t st) {
@@ -513,6 +608,16 @@ int launch_gather(int storage, const Geom& g, const IterBufs& b, const IterParam
         case 0: return launch_gather_t<float>(g, b, p, sc, w, st);
         case 1: return launch_gather_t<__nv_bfloat16>(g, b, p, sc, w, st);
         case 2: return launch_gather_t<__half>(g, b, p, sc, w, st);
+    }
+    return -1;
+}
+
+int launch_window(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
+                  const L1Work& w, int part_cap, cudaStream_t st) {
+    switch (storage) {
+        case 0: return launch_window_t<float>(g, b, p, sc, w, part_cap, st);
+        case 1: return launch_window_t<__nv_bfloat16>(g, b, p, sc, w, part_cap, st);
+        case 2: return launch_window_t<__half>(g, b, p, sc, w, part_cap, st);
     }
     return -1;
 }

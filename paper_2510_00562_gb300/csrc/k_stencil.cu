@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(NT, 2) k1_stencil(const K1Args<T> a) {
     const long long cube = g.cube;
     const long long plane = (long long)g.n1 * g.p2;
     const float cs = (float)(1.0 - a.sc->c[P.parity]);   // y4 = (1 - c) q
+    const unsigned it32 = (unsigned)a.sc->iter;           // seeds the 16-bit rounding streams
 
     // window of the l1 search for s (v = 0) and t (v = 1)
     const bool win_s = !P.tau_exact && a.sc->radius[0] > 0.0 && a.sc->ctl[0].window_ok;
@@ -166,7 +167,11 @@ __global__ void __launch_bounds__(NT, 2) k1_stencil(const K1Args<T> a) {
         const float un = fminf(fmaxf(u - P.gamma_u * (d1 + dst + y4), P.mu_lo), P.mu_hi);
         up[slot * C_PL + kc] = 2.f * un - u;
         gs[kc] = gcur;
-        if (store && r < TY && c < TX) stT(a.u_n + g.at(bb, gi, gj), un);
+        if (store && r < TY && c < TX) {
+            const long long o = g.at(bb, gi, gj);
+            SRStream sr((unsigned)o, it32, 2u);
+            stS(a.u_n + o, un, sr);
+        }
     };
     // w steps at (r, c) in [-1, TY] x [-1, TX], band b
     auto w_item = [&](int b, int r, int c) {
@@ -200,6 +205,7 @@ __global__ void __launch_bounds__(NT, 2) k1_stencil(const K1Args<T> a) {
             const float gam = set ? P.gamma_w2 : P.gamma_w1;
             const float thr = set ? P.thr_w2 : P.thr_w1;
             T* dst = set ? a.w2_n : a.w1_n;
+            SRStream sr((unsigned)g.at(b, gi, gj), it32, 4u + set);
 #pragma unroll
             for (int gr = 0; gr < 3; ++gr) {
                 float* pv = ws + (6 * set + 2 * gr) * W_PL + kw;
@@ -213,8 +219,8 @@ __global__ void __launch_bounds__(NT, 2) k1_stencil(const K1Args<T> a) {
                 *ph = 2.f * nh - wh;
                 if (inner) {
                     const long long o = g.at(b, gi, gj);
-                    stT(dst + (2 * gr) * cube + o, nv);
-                    stT(dst + (2 * gr + 1) * cube + o, nh);
+                    stS(dst + (2 * gr) * cube + o, nv, sr);
+                    stS(dst + (2 * gr + 1) * cube + o, nh, sr);
                 }
             }
         }
@@ -314,10 +320,11 @@ __global__ void __launch_bounds__(NT, 2) k1_stencil(const K1Args<T> a) {
                 const int ky = (r + 2) * SW + (c + 4);
                 const int slot = b & 1;
                 const long long o = g.at(b, gi, gj);
-                stT(a.y1_n + o, Yp(slot, 0)[ky] + P.gamma_y1 * (duv - gv[0]));
-                stT(a.y1_n + cube + o, Yp(slot, 1)[ky] + P.gamma_y1 * (duh - gh[0]));
-                stT(a.y2_n + o, Yp(slot, 2)[ky] + P.gamma_y2 * (ddv - gv[1]));
-                stT(a.y2_n + cube + o, Yp(slot, 3)[ky] + P.gamma_y2 * (ddh - gh[1]));
+                SRStream sr((unsigned)o, it32, 3u);
+                stS(a.y1_n + o, Yp(slot, 0)[ky] + P.gamma_y1 * (duv - gv[0]), sr);
+                stS(a.y1_n + cube + o, Yp(slot, 1)[ky] + P.gamma_y1 * (duh - gh[0]), sr);
+                stS(a.y2_n + o, Yp(slot, 2)[ky] + P.gamma_y2 * (ddv - gv[1]), sr);
+                stS(a.y2_n + cube + o, Yp(slot, 3)[ky] + P.gamma_y2 * (ddh - gh[1]), sr);
                 if (win_s || win_t) {
                     const float qv = qs[slot * U_PL + r * SW + (c + 4)];
                     const long long oi = bo + (long long)gi * g.p2 + gj;
@@ -394,13 +401,14 @@ __global__ void __launch_bounds__(NT, 2) k1_stencil(const K1Args<T> a) {
         const unsigned m = __ldcg(&a.sc->acc[v].m);
         const double tlo = C.theta_lo, thi = C.theta_hi;
         double tau = 0.0;
-        const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u);
+        WinInfo wi;
+        const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi);
         if (tid == 0) {
             if (!miss) {
                 l1_record_tau(C, tau, (double)min(m, kCandCap), thi - tlo);
                 C.hits++;
             } else {
-                C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0; C.exact_runs++;
+                l1_after_miss(C, miss, wi, (double)n, m, tlo, thi);
             }
             a.sc->acc[v].m = 0;
         }

@@ -140,6 +140,7 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
     float* gs = reinterpret_cast<float*>(sm + L::OFF_G);
     const int bstart = max(b0 - 1, 0);
     const int blast = min(b1, g.n3 - 1);
+    const unsigned it32 = (unsigned)a.sc->iter;     // seeds the 16-bit rounding streams
 
     auto yg = [&](int band) { return sm + ((band - bstart) % L::NYS) * L::YG_B; };
     auto wg = [&](int band) { return sm + L::OFF_WG + ((band - b0) % L::NWS) * L::WG_B; };
@@ -222,7 +223,10 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
         const float un = fminf(fmaxf(u - P.gamma_u * (d1 + dst + y4), P.mu_lo), P.mu_hi);
         upb[kc] = 2.f * un - u;
         gs[kc] = gcur;
-        if (o >= 0) stT(a.u_n + o, un);
+        if (o >= 0) {
+            SRStream sr((unsigned)o, it32, 2u);
+            stS(a.u_n + o, un, sr);
+        }
     };
     // w step of one set (0: w1, 1: w2; a compile-time constant) at (r, c) in
     // [-1, TY] x [-1, TX] of the band whose y-group is `ysl` and whose w slot is
@@ -266,6 +270,7 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
         const float thr = set ? P.thr_w2 : P.thr_w1;
         const float thr2 = thr * thr;
         T* dst = (set ? a.w2_n : a.w1_n) + (o >= 0 ? o : 0);
+        SRStream sr((unsigned)(o >= 0 ? o : 0), it32, 4u + set);
 #pragma unroll
         for (int gr = 0; gr < 3; ++gr) {
             const int kv = 6 * set + 2 * gr;
@@ -278,8 +283,8 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
             Wp(band, kv)[kp] = 2.f * nv - wv;
             Wp(band, kv + 1)[kp] = 2.f * nh - wh;
             if (o >= 0) {
-                stT(dst + (2 * gr) * cube, nv);
-                stT(dst + (2 * gr + 1) * cube, nh);
+                stS(dst + (2 * gr) * cube, nv, sr);
+                stS(dst + (2 * gr + 1) * cube, nh, sr);
             }
         }
     };
@@ -359,10 +364,11 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
                              : 0.f;
             }
             const int ky = (r + 2) * SW + (c + OX);
-            stT(a.y1_n + ob, sld(Yp(ysl, 0) + ky) + P.gamma_y1 * (duv - gv[0]));
-            stT(a.y1_n + cube + ob, sld(Yp(ysl, 1) + ky) + P.gamma_y1 * (duh - gh[0]));
-            stT(a.y2_n + ob, sld(Yp(ysl, 2) + ky) + P.gamma_y2 * (ddv - gv[1]));
-            stT(a.y2_n + cube + ob, sld(Yp(ysl, 3) + ky) + P.gamma_y2 * (ddh - gh[1]));
+            SRStream sr((unsigned)ob, it32, 3u);
+            stS(a.y1_n + ob, sld(Yp(ysl, 0) + ky) + P.gamma_y1 * (duv - gv[0]), sr);
+            stS(a.y1_n + cube + ob, sld(Yp(ysl, 1) + ky) + P.gamma_y1 * (duh - gh[0]), sr);
+            stS(a.y2_n + ob, sld(Yp(ysl, 2) + ky) + P.gamma_y2 * (ddv - gv[1]), sr);
+            stS(a.y2_n + cube + ob, sld(Yp(ysl, 3) + ky) + P.gamma_y2 * (ddh - gh[1]), sr);
             if (win_s || win_t) {
                 const T* q = reinterpret_cast<const T*>(ysl + L::O_Q);
                 const T* sp = reinterpret_cast<const T*>(ysl + L::O_S);
@@ -541,13 +547,14 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
         const unsigned m = __ldcg(&a.sc->acc[v].m);
         const double tlo = C.theta_lo, thi = C.theta_hi;
         double tau = 0.0;
-        const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u);
+        WinInfo wi;
+        const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi);
         if (tid == 0) {
             if (!miss) {
                 l1_record_tau(C, tau, (double)min(m, kCandCap), thi - tlo);
                 C.hits++;
             } else {
-                C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0; C.exact_runs++;
+                l1_after_miss(C, miss, wi, (double)n, m, tlo, thi);
             }
             a.sc->acc[v].m = 0;
         }
