@@ -111,7 +111,9 @@ void gsstv_default_params(gsstv_params* p);
 
 /* Creates a solver for N1 x N2 x N3 cubes.  Allocates and zeroes the whole
  * iterate state on the current device (about 43 cube-sized buffers of the
- * storage type plus a float32 copy of v).  stream: cudaStream_t or NULL. */
+ * storage type plus a float32 copy of v).  stream: cudaStream_t or NULL.
+ * Limits: N1, N2 <= 2^20, N3 <= 2^16 and 6 * N1 * N3 * (N2 rounded up to 8)
+ * < 2^32 (about 715 M voxels); larger shapes return GSSTV_ERR_ARG. */
 int gsstv_create(gsstv_handle** h, int n1, int n2, int n3,
                  const gsstv_params* p, void* stream);
 

@@ -273,6 +273,8 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
     h->g.n1 = n1; h->g.n2 = n2; h->g.n3 = n3;
     h->g.p2 = ((n2 + 7) / 8) * 8;
     h->g.cube = (long long)n3 * n1 * h->g.p2;
+    // the stencil kernel addresses up to six stacked cubes with 32-bit offsets
+    if (h->g.cube * 6 >= (1ll << 32)) { delete h; return GSSTV_ERR_ARG; }
     const size_t cb = (size_t)h->g.cube * h->esz;
     int rc = GSSTV_OK;
     for (int k = 0; k < 2 && rc == GSSTV_OK; ++k) {
@@ -290,11 +292,14 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->v, (size_t)h->g.cube * sizeof(float));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->sc, sizeof(Scal));
     if (rc == GSSTV_OK && (k1_configure(p->storage) != 0 || light_configure(p->storage) != 0 ||
-                           k1_tma_configure(p->storage) != 0))
+                           (p->storage == GSSTV_FP32 && k1_tma_configure(p->storage) != 0)))
         rc = GSSTV_ERR_CUDA;
     {
-        const char* ev = std::getenv("GSSTV_K1");   // debugging aid: pick the K1 variant
-        h->k1_variant = (ev && std::strcmp(ev, "coop") == 0) ? 0 : 1;
+        // The TMA-fed K1 serves float32 storage; 16-bit storage runs the
+        // cooperative-load K1.  GSSTV_K1=coop (a debugging aid) selects the
+        // cooperative kernel for float32 too.
+        const char* ev = std::getenv("GSSTV_K1");
+        h->k1_variant = (p->storage == GSSTV_FP32 && !(ev && std::strcmp(ev, "coop") == 0)) ? 1 : 0;
     }
     h->k1_ctas = std::max(k1_grid_ctas(h->g), k1_tma_ctas(h->g));
     h->k2_cap = k2_grid_ctas(h->g);
@@ -310,7 +315,7 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
         for (auto& e : h->ev)
             if (rc == GSSTV_OK && cudaEventCreate(&e) != cudaSuccess) { e = nullptr; rc = GSSTV_ERR_CUDA; }
     }
-    for (int par = 0; par < 2 && rc == GSSTV_OK; ++par) {
+    for (int par = 0; par < 2 && rc == GSSTV_OK && h->k1_variant == 1; ++par) {
         const IterBufs b = bufs(h, par);
         if (k1_tma_maps(p->storage, h->g, b, &h->maps[par]) != 0) rc = GSSTV_ERR_CUDA;
     }

@@ -130,10 +130,12 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
                                         float lo_s, float hi_s, float lo_t, float hi_t, float cs) {
     using L = Lay<T>;
     constexpr int TY = L::TY, TX = L::TX, SW = L::SW, OX = L::OX, UC = L::UC;
+    constexpr int WP_ROW = L::kInPlace ? SW : L::WPC;
     const Geom& g = a.g;
     const IterParams& P = a.p;
     const int tid = threadIdx.x;
-    const long long cube = g.cube;
+    const unsigned cube = (unsigned)g.cube;        // < 2^31 (checked at handle creation)
+    const unsigned plane = (unsigned)g.n1 * (unsigned)g.p2;
     uint64_t* ybar = reinterpret_cast<uint64_t*>(sm + L::OFF_BAR);
     uint64_t* wbar = ybar + L::NYS;
     float* up = reinterpret_cast<float*>(sm + L::OFF_UP);
@@ -142,22 +144,21 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
     const int blast = min(b1, g.n3 - 1);
     const unsigned it32 = (unsigned)a.sc->iter;     // seeds the 16-bit rounding streams
 
+    // ---- ring slots (computed once per band by the callers below) ----
     auto yg = [&](int band) { return sm + ((band - bstart) % L::NYS) * L::YG_B; };
     auto wg = [&](int band) { return sm + L::OFF_WG + ((band - b0) % L::NWS) * L::WG_B; };
-    auto Yp = [&](const unsigned char* slot, int pl) { return reinterpret_cast<const T*>(slot + pl * L::Y_B); };
-    // w (staged, type T) and w' (float, in place for FP32)
-    auto Wst = [&](const unsigned char* slot, int k) { return reinterpret_cast<const T*>(slot + k * L::W_B); };
     // w' of a band: in place in its w slot (FP32), else in one of two float
     // planes that alternate with the band (16-bit storage)
-    auto Wp = [&](int band, int k) -> float* {
-        if constexpr (L::kInPlace) return reinterpret_cast<float*>(wg(band) + k * L::W_B);
-        else return reinterpret_cast<float*>(sm + L::OFF_WP + ((band - b0) & 1) * L::WP1_B) + k * (L::WR * L::WPC);
+    auto wpl = [&](int band) -> float* {
+        if constexpr (L::kInPlace) return reinterpret_cast<float*>(wg(band));
+        else return reinterpret_cast<float*>(sm + L::OFF_WP + ((band - b0) & 1) * L::WP1_B);
     };
+    constexpr int WP_PL = L::kInPlace ? L::W_B / 4 : L::WR * L::WPC;   // floats between w' planes
+    auto upl = [&](int band) { return up + (band % L::NUS) * L::UP1; };
     auto wp_idx = [&](int r, int c) {
         if constexpr (L::kInPlace) return (r + 1) * SW + (c + OX);
         else return (r + 1) * L::WPC + (c + 1);
     };
-    constexpr int WP_ROW = L::kInPlace ? SW : L::WPC;
 
     auto issue_y = [&](int band) {
         unsigned char* s = yg(band);
@@ -186,12 +187,9 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
         return mbar_wait(ybar + (band - bstart) % L::NYS, ((band - bstart) / L::NYS) & 1);
     };
     auto wait_w = [&](int band) { return mbar_wait(wbar + (band - b0) % L::NWS, ((band - b0) / L::NWS) & 1); };
-    auto upl = [&](int band) { return up + (band % L::NUS) * L::UP1; };
 
-    // D^T y = D_v^T y_v + D_h^T y_h at tile-relative (r, c), from a y-group slot
-    auto dty = [&](const unsigned char* slot, int pv, int r, int c) {
-        const T* yv = Yp(slot, pv);
-        const T* yh = Yp(slot, pv + 1);
+    // D^T y = D_v^T y_v + D_h^T y_h at tile-relative (r, c); yv, yh: y planes
+    auto dty = [&](const T* yv, const T* yh, int r, int c) {
         const int k = (r + 2) * SW + (c + OX);
         if constexpr (EDGE) {
             const int gi = i0 + r, gj = j0 + c;
@@ -205,50 +203,49 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
             return ((sld(yv + k - SW) - sld(yv + k)) + sld(yh + k - 1)) - sld(yh + k);
         }
     };
-    // u step and u' of band bb at (r, c) in [0, TY] x [0, TX]
-    auto u_item = [&](const unsigned char* slot, int bb, int r, int c, long long o) {
+    // u step and u' of band bb at (r, c) in [0, TY] x [0, TX]; ys: y-group of
+    // bb; upb: u' plane of bb; dst: u+ of this voxel, or null (no store)
+    auto u_item = [&](const unsigned char* ys, float* upb, int bb, int r, int c, T* dst) {
         const int kc = r * UC + c;
-        float* upb = upl(bb);
         if constexpr (EDGE) {
             if (i0 + r >= g.n1 || j0 + c >= g.n2) { upb[kc] = 0.f; gs[kc] = 0.f; return; }
         }
-        const float d1 = dty(slot, 0, r, c);
-        const float gcur = dty(slot, 2, r, c);
-        float dst = 0.f;
-        if (bb >= 1) dst += gs[kc];
-        if (bb <= g.n3 - 2) dst -= gcur;
+        const T* yp = reinterpret_cast<const T*>(ys);
+        const float d1 = dty(yp, yp + L::Y_B / L::ES, r, c);
+        const float gcur = dty(yp + 2 * (L::Y_B / L::ES), yp + 3 * (L::Y_B / L::ES), r, c);
+        float dst_ = 0.f;
+        if (bb >= 1) dst_ += gs[kc];
+        if (bb <= g.n3 - 2) dst_ -= gcur;
         const int ku = r * SW + (c + OX);
-        const float y4 = cs * sld(reinterpret_cast<const T*>(slot + L::O_Q) + ku);
-        const float u = sld(reinterpret_cast<const T*>(slot + L::O_U) + ku);
-        const float un = fminf(fmaxf(u - P.gamma_u * (d1 + dst + y4), P.mu_lo), P.mu_hi);
+        const float y4 = cs * sld(reinterpret_cast<const T*>(ys + L::O_Q) + ku);
+        const float u = sld(reinterpret_cast<const T*>(ys + L::O_U) + ku);
+        const float un = fminf(fmaxf(u - P.gamma_u * (d1 + dst_ + y4), P.mu_lo), P.mu_hi);
         upb[kc] = 2.f * un - u;
         gs[kc] = gcur;
-        if (o >= 0) {
-            SRStream sr((unsigned)o, it32, 2u);
-            stS(a.u_n + o, un, sr);
+        if (dst) {
+            SRStream sr((unsigned)(dst - a.u_n), it32, 2u);
+            stS(dst, un, sr);
         }
     };
-    // w step of one set (0: w1, 1: w2; a compile-time constant) at (r, c) in
-    // [-1, TY] x [-1, TX] of the band whose y-group is `ysl` and whose w slot is
-    // `wsl`; `o` is the global offset of the voxel when (r, c) is a tile voxel
-    // (w+ is stored) and -1 on the ring.
-    auto w_item = [&](auto set_c, int band, const unsigned char* ysl, int r, int c, long long o) {
+    // w step of one set (a compile-time constant: 0 = w1, 1 = w2) at (r, c)
+    // in [-1, TY] x [-1, TX]; ys: y-group, wst: staged w planes, wp: w' planes
+    // of the band; dst: w+ of this voxel (set's first plane), or null on the ring
+    auto w_item = [&](auto set_c, const unsigned char* ys, const T* wst, float* wp, int r, int c, T* dst) {
         constexpr int set = decltype(set_c)::value;
-        const unsigned char* wsl = wg(band);
         const int kw = (r + 1) * SW + (c + OX);
         const int kp = wp_idx(r, c);
         const int gi = i0 + r, gj = j0 + c;
         if constexpr (EDGE) {
             if (gi < 0 || gi >= g.n1 || gj < 0 || gj >= g.n2) {
 #pragma unroll
-                for (int k = 6 * set; k < 6 * set + 6; ++k) Wp(band, k)[kp] = 0.f;
+                for (int k = 6 * set; k < 6 * set + 6; ++k) wp[k * WP_PL + kp] = 0.f;
                 return;
             }
         }
         const bool mv = !EDGE || gi < g.n1 - 1, mh = !EDGE || gj < g.n2 - 1;
         const int ky = (r + 2) * SW + (c + OX);
-        const T* yv = reinterpret_cast<const T*>(ysl + (2 * set) * L::Y_B) + ky;
-        const T* yh = reinterpret_cast<const T*>(ysl + (2 * set + 1) * L::Y_B) + ky;
+        const T* yv = reinterpret_cast<const T*>(ys + (2 * set) * L::Y_B) + ky;
+        const T* yh = reinterpret_cast<const T*>(ys + (2 * set + 1) * L::Y_B) + ky;
         auto V = [&](int dr, int dc) {
             if constexpr (EDGE) return (gi + dr == g.n1 - 1) ? 0.f : sld(yv + dr * SW + dc);
             else return sld(yv + dr * SW + dc);
@@ -269,20 +266,20 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
         const float gam = set ? P.gamma_w2 : P.gamma_w1;
         const float thr = set ? P.thr_w2 : P.thr_w1;
         const float thr2 = thr * thr;
-        T* dst = (set ? a.w2_n : a.w1_n) + (o >= 0 ? o : 0);
-        SRStream sr((unsigned)(o >= 0 ? o : 0), it32, 4u + set);
+        SRStream sr(dst ? (unsigned)(dst - (set ? a.w2_n : a.w1_n)) : 0u, it32, 4u + set);
 #pragma unroll
         for (int gr = 0; gr < 3; ++gr) {
             const int kv = 6 * set + 2 * gr;
-            const float wv = sld(Wst(wsl, kv) + kw), wh = sld(Wst(wsl, kv + 1) + kw);
+            const float wv = sld(wst + kv * (L::W_B / L::ES) + kw);
+            const float wh = sld(wst + (kv + 1) * (L::W_B / L::ES) + kw);
             const float xv = wv + gam * Lv[gr], xh = wh + gam * Lh[gr];
             // Eq. 24: max(1 - thr / ||x||, 0) x, with 1 / ||x|| from rsqrt
             const float n2 = xv * xv + xh * xh;
             const float sc = n2 > thr2 ? fmaxf(1.f - thr * rsqrtf(n2), 0.f) : 0.f;
             const float nv = sc * xv, nh = sc * xh;
-            Wp(band, kv)[kp] = 2.f * nv - wv;
-            Wp(band, kv + 1)[kp] = 2.f * nh - wh;
-            if (o >= 0) {
+            wp[kv * WP_PL + kp] = 2.f * nv - wv;
+            wp[(kv + 1) * WP_PL + kp] = 2.f * nh - wh;
+            if (dst) {
                 stS(dst + (2 * gr) * cube, nv, sr);
                 stS(dst + (2 * gr + 1) * cube, nh, sr);
             }
@@ -290,45 +287,43 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
     };
     using Set0 = std::integral_constant<int, 0>;
     using Set1 = std::integral_constant<int, 1>;
-    // positions of the one-pixel ring around the tile: w has a ring on all four
-    // sides (2 (TX + 2) + 2 TY positions), u' only below and to the right
-    auto w_ring = [&](int k, int& r, int& c) {
-        if (k < TX + 2) { r = -1; c = k - 1; return; }
-        k -= TX + 2;
-        if (k < TX + 2) { r = TY; c = k - 1; return; }
-        k -= TX + 2;
-        if (k < TY) { r = k; c = -1; return; }
-        r = k - TY; c = TX;
-    };
-    auto u_ring = [&](int k, int& r, int& c) {
-        if (k < TX + 1) { r = TY; c = k; return; }
-        r = k - (TX + 1); c = TX;
-    };
-    constexpr int NWR = 2 * (TX + 2) + 2 * TY;        // ring w positions
-    constexpr int NUR = (TX + 1) + TY;                // ring u' positions
-    static_assert(2 * NWR + NUR <= L::NT, "ring work fits one round");
-    // ---- this thread's tile voxel and its share of the ring ----
+
+    // ---- this thread's tile voxel and its share of the one-pixel ring ----
     const int r_t = tid / TX, c_t = tid - (tid / TX) * TX;
     const int gi_t = i0 + r_t, gj_t = j0 + c_t;
     const bool valid_t = !EDGE || (gi_t < g.n1 && gj_t < g.n2);
-    const long long plane = (long long)g.n1 * g.p2;
-    const long long o_t = valid_t ? (long long)gi_t * g.p2 + gj_t : 0;   // offset inside a band
-    // ring work: threads [0, 2 NWR) take one (position, set) half of a ring w
-    // item, threads [2 NWR, 2 NWR + NUR) one ring u' item
-    int rw_r = 0, rw_c = 0, rw_set = 0, ru_r = 0, ru_c = 0;
-    const bool has_rw = tid < 2 * NWR;
-    const bool has_ru = !has_rw && tid < 2 * NWR + NUR;
-    if (has_rw) { w_ring(tid >> 1, rw_r, rw_c); rw_set = tid & 1; }
-    if (has_ru) u_ring(tid - 2 * NWR, ru_r, ru_c);
+    const unsigned o_t = valid_t ? (unsigned)gi_t * (unsigned)g.p2 + (unsigned)gj_t : 0u;
+    // ring w positions: 2 (TX + 2) + 2 TY; each set takes four warps (128
+    // threads, one position each) so a warp never mixes the two sets; ring u'
+    // positions ((TX + 1) + TY) go to the next warps
+    constexpr int NWR = 2 * (TX + 2) + 2 * TY;
+    constexpr int NUR = (TX + 1) + TY;
+    static_assert(NWR <= 128 && 256 + NUR <= L::NT, "ring work layout");
+    int rw_r = 0, rw_c = 0, ru_r = 0, ru_c = 0;
+    const int rw_set = tid >> 7;                       // 0 or 1 for tid < 256
+    const bool has_rw = tid < 256 && (tid & 127) < NWR;
+    const bool has_ru = tid >= 256 && tid < 256 + NUR;
+    if (has_rw) {
+        int k = tid & 127;
+        if (k < TX + 2) { rw_r = -1; rw_c = k - 1; }
+        else if ((k -= TX + 2) < TX + 2) { rw_r = TY; rw_c = k - 1; }
+        else if ((k -= TX + 2) < TY) { rw_r = k; rw_c = -1; }
+        else { rw_r = k - TY; rw_c = TX; }
+    }
+    if (has_ru) {
+        const int k = tid - 256;
+        if (k < TX + 1) { ru_r = TY; ru_c = k; } else { ru_r = k - (TX + 1); ru_c = TX; }
+    }
 
     // ---- dual ascent of y1, y2 and the l1 window statistics of one band ----
-    // Reads w' (complete), u' of this band and the next, and the band's y-group.
+    // Reads the band's completed w', u' of the band and the next, its y-group.
     auto t_item = [&](int band) {
         const bool nxt = band + 1 < g.n3;
         const float* upb = upl(band);
         const float* upn = upl(band + 1);
-        const unsigned char* ysl = yg(band);
-        const long long ob = (long long)band * plane + o_t;
+        const unsigned char* ys = yg(band);
+        const float* wp = wpl(band);
+        const unsigned ob = (unsigned)band * plane + o_t;
         float xs = 0.f, xt = 0.f;
         if (valid_t) {
             const int r = r_t, c = c_t;
@@ -343,11 +338,11 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
                 if (mv) ddv = (upn[kc + UC] - upb[kc + UC]) - d0;
                 if (mh) ddh = (upn[kc + 1] - upb[kc + 1]) - d0;
             }
-            const int kp = wp_idx(r, c);
+            const float* wk = wp + wp_idx(r, c);
             float gv[2], gh[2];
 #pragma unroll
             for (int set = 0; set < 2; ++set) {
-                auto Wk = [&](int k, int dr, int dc) { return Wp(band, 6 * set + k)[kp + dr * WP_ROW + dc]; };
+                auto Wk = [&](int k, int dr, int dc) { return wk[(6 * set + k) * WP_PL + dr * WP_ROW + dc]; };
                 auto A_ = [&](int dr, int dc) {
                     if constexpr (EDGE) return (gi_t + dr < g.n1 - 1) ? Wk(1, dr, dc) : 0.f;
                     else return Wk(1, dr, dc);
@@ -364,16 +359,18 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
                              : 0.f;
             }
             const int ky = (r + 2) * SW + (c + OX);
-            SRStream sr((unsigned)ob, it32, 3u);
-            stS(a.y1_n + ob, sld(Yp(ysl, 0) + ky) + P.gamma_y1 * (duv - gv[0]), sr);
-            stS(a.y1_n + cube + ob, sld(Yp(ysl, 1) + ky) + P.gamma_y1 * (duh - gh[0]), sr);
-            stS(a.y2_n + ob, sld(Yp(ysl, 2) + ky) + P.gamma_y2 * (ddv - gv[1]), sr);
-            stS(a.y2_n + cube + ob, sld(Yp(ysl, 3) + ky) + P.gamma_y2 * (ddh - gh[1]), sr);
+            const T* yp = reinterpret_cast<const T*>(ys) + ky;
+            constexpr int YPL = L::Y_B / L::ES;
+            SRStream sr(ob, it32, 3u);
+            stS(a.y1_n + ob, sld(yp) + P.gamma_y1 * (duv - gv[0]), sr);
+            stS(a.y1_n + cube + ob, sld(yp + YPL) + P.gamma_y1 * (duh - gh[0]), sr);
+            stS(a.y2_n + ob, sld(yp + 2 * YPL) + P.gamma_y2 * (ddv - gv[1]), sr);
+            stS(a.y2_n + cube + ob, sld(yp + 3 * YPL) + P.gamma_y2 * (ddh - gh[1]), sr);
             if (win_s || win_t) {
-                const T* q = reinterpret_cast<const T*>(ysl + L::O_Q);
-                const T* sp = reinterpret_cast<const T*>(ysl + L::O_S);
-                const T* tp = reinterpret_cast<const T*>(ysl + L::O_T);
-                const T* y3p = reinterpret_cast<const T*>(ysl + L::O_Y3);
+                const T* q = reinterpret_cast<const T*>(ys + L::O_Q);
+                const T* sp = reinterpret_cast<const T*>(ys + L::O_S);
+                const T* tp = reinterpret_cast<const T*>(ys + L::O_T);
+                const T* y3p = reinterpret_cast<const T*>(ys + L::O_Y3);
                 const float qv = sld(q + r * SW + (c + OX));
                 const float y3v = sld(y3p + (r + 1) * TX + c);
                 const float y3u = (!EDGE || gi_t >= 1) ? sld(y3p + r * TX + c) : 0.f;
@@ -403,11 +400,11 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
     bool ok = true;
     if (b0 >= 1) {
         ok = wait_y(b0 - 1);
-        const unsigned char* slot = yg(b0 - 1);
+        const T* yp = reinterpret_cast<const T*>(yg(b0 - 1));
         for (int e = tid; e < L::UR * UC; e += L::NT) {
             const int r = e / UC, c = e - r * UC;
             if (EDGE && (i0 + r >= g.n1 || j0 + c >= g.n2)) { gs[e] = 0.f; continue; }
-            gs[e] = dty(slot, 2, r, c);
+            gs[e] = dty(yp + 2 * (L::Y_B / L::ES), yp + 3 * (L::Y_B / L::ES), r, c);
         }
     }
     ok = wait_y(b0) && ok;
@@ -415,8 +412,9 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
     if (!ok) return false;
     {
         const unsigned char* ys0 = yg(b0);
-        u_item(ys0, b0, r_t, c_t, valid_t ? (long long)b0 * plane + o_t : -1);
-        if (has_ru) u_item(ys0, b0, ru_r, ru_c, -1);
+        float* up0 = upl(b0);
+        u_item(ys0, up0, b0, r_t, c_t, valid_t ? a.u_n + ((unsigned)b0 * plane + o_t) : nullptr);
+        if (has_ru) u_item(ys0, up0, b0, ru_r, ru_c, nullptr);
     }
     __syncthreads();
 
@@ -430,18 +428,21 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
         }
         bool okb = wait_w(b);
         if (has_next) okb = wait_y(b + 1) && okb;
-        const long long ob = valid_t ? (long long)b * plane + o_t : -1;
-        const unsigned char* ysl = yg(b);
-        const unsigned char* ysn = yg(b + 1);
         if (okb) {
-            w_item(Set0{}, b, ysl, r_t, c_t, ob);
-            w_item(Set1{}, b, ysl, r_t, c_t, ob);
-            if (has_next) u_item(ysn, b + 1, r_t, c_t, (valid_t && b + 1 < b1) ? ob + plane : -1);
+            const unsigned char* ys = yg(b);
+            const unsigned char* ysn = yg(b + 1);
+            const T* wst = reinterpret_cast<const T*>(wg(b));
+            float* wp = wpl(b);
+            float* upn = upl(b + 1);
+            const unsigned ob = (unsigned)b * plane + o_t;
+            w_item(Set0{}, ys, wst, wp, r_t, c_t, valid_t ? a.w1_n + ob : nullptr);
+            w_item(Set1{}, ys, wst, wp, r_t, c_t, valid_t ? a.w2_n + ob : nullptr);
+            if (has_next) u_item(ysn, upn, b + 1, r_t, c_t, (valid_t && b + 1 < b1) ? a.u_n + (ob + plane) : nullptr);
             if (has_rw) {
-                if (rw_set == 0) w_item(Set0{}, b, ysl, rw_r, rw_c, -1);
-                else w_item(Set1{}, b, ysl, rw_r, rw_c, -1);
+                if (rw_set == 0) w_item(Set0{}, ys, wst, wp, rw_r, rw_c, nullptr);
+                else w_item(Set1{}, ys, wst, wp, rw_r, rw_c, nullptr);
             }
-            if (has_ru && has_next) u_item(ysn, b + 1, ru_r, ru_c, -1);
+            if (has_ru && has_next) u_item(ysn, upn, b + 1, ru_r, ru_c, nullptr);
         }
         if (b > b0) t_item(b - 1);
         // the slots freed at this step are reloaded by TMA at the next one:
@@ -594,19 +595,19 @@ int k1_tma_ctas(const Geom& g) {
     return tx * ty * ((g.n3 + chunk - 1) / chunk);
 }
 
+// The TMA-fed kernel is built for float32 storage only (16-bit storage runs
+// the cooperative-load kernel of k_stencil.cu).
 int k1_tma_configure(int storage) {
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (storage) {
-        case 0: e = cudaFuncSetAttribute(k1_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay<float>::SMEM); break;
-        case 1: e = cudaFuncSetAttribute(k1_tma<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay<__nv_bfloat16>::SMEM); break;
-        case 2: e = cudaFuncSetAttribute(k1_tma<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay<__half>::SMEM); break;
-    }
+    if (storage != 0) return -1;
+    const cudaError_t e =
+        cudaFuncSetAttribute(k1_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay<float>::SMEM);
     return e == cudaSuccess ? 0 : -3;
 }
 
 // tensor maps over the current-parity buffers of one iteration
 int k1_tma_maps(int storage, const Geom& g, const IterBufs& b, K1Maps* m) {
-    const int es = storage == 0 ? 4 : 2;
+    if (storage != 0) return -1;
+    const int es = 4;
     const int ox = 16 / es, sw = 32 + 2 * ox;
     int rc = 0;
     rc |= tma_encode_cubes(&m->y1, b.y1, es, g.n1, g.n2, g.n3, g.p2, 2, sw, 16 + 4);
@@ -623,12 +624,7 @@ int k1_tma_maps(int storage, const Geom& g, const IterBufs& b, K1Maps* m) {
 
 int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p,
                   Scal* sc, const L1Work& w, cudaStream_t st) {
-    switch (storage) {
-        case 0: return launch_k1_tma_t<float>(g, m, b, p, sc, w, st);
-        case 1: return launch_k1_tma_t<__nv_bfloat16>(g, m, b, p, sc, w, st);
-        case 2: return launch_k1_tma_t<__half>(g, m, b, p, sc, w, st);
-    }
-    return -1;
+    return storage == 0 ? launch_k1_tma_t<float>(g, m, b, p, sc, w, st) : -1;
 }
 
 }  // namespace gsstv

@@ -280,10 +280,30 @@ def test_nonfinite_observation_is_reported():
 
 
 def test_out_of_memory_is_reported():
+    """Handles of the largest accepted cube (8192 x 8192 x 10 voxels, ~115 GB of
+    FP32 state each) until the device runs out: the failing create returns
+    GSSTV_ERR_OOM, leaks nothing, and the device stays usable."""
+    from paper_2510_00562_gb300 import binding as B
+    held, code = [], None
+    try:
+        for _ in range(4):
+            try:
+                held.append(GeoSSTVSolver(8192, 8192, 10, make_params()))
+            except B.GsstvError as e:
+                code = e.code
+                break
+    finally:
+        for h in held:
+            h.close()
+    assert code == B.GSSTV_ERR_OOM
+    free, _ = torch.cuda.mem_get_info()
+    assert free > 200 * 2**30
+    with GeoSSTVSolver(8, 8, 2, make_params(max_iter=2)) as sol:
+        sol.solve(to_dev(np.full((2, 8, 8), 0.5, np.float32)))
+
+
+def test_oversized_cube_is_refused():
     from paper_2510_00562_gb300 import binding as B
     with pytest.raises(B.GsstvError) as ei:
         GeoSSTVSolver(1 << 20, 1 << 14, 4096, make_params())
-    assert ei.value.code == B.GSSTV_ERR_OOM
-    # the device is still usable afterwards
-    with GeoSSTVSolver(8, 8, 2, make_params(max_iter=2)) as sol:
-        sol.solve(to_dev(np.full((2, 8, 8), 0.5, np.float32)))
+    assert ei.value.code == B.GSSTV_ERR_ARG

@@ -60,3 +60,27 @@ def test_mixed_then_fp32_refinement(problem, storage):
           f"+{iters - n16} FP32 passes: err {errs}, MPSNR {mref:.4f}; FP32 alone {m32:.4f}")
     assert abs(mref - m32) <= 0.01
     assert max(errs.values()) < 1e-2
+
+
+@pytest.mark.parametrize("storage,tol", [("bf16", 2e-2), ("fp16", 3e-3)])
+@pytest.mark.parametrize("shape", [(70, 100, 20), (64, 96, 40)])
+def test_one_pass_16bit_storage(shape, storage, tol):
+    """One pass from a random state with 16-bit storage, on cubes that have
+    interior tiles (the stencil kernel's unmasked path) as well as border
+    tiles: every variable within the 16-bit rounding of the inputs and outputs
+    (BF16 8 bits, FP16 11 bits of mantissa) of the FP64 oracle's pass."""
+    n1, n2, n3 = shape
+    rs = synth.random_state(n1, n2, n3, seed=3, scale=0.1)
+    v = np.random.default_rng(8).uniform(0, 1, size=(n3, n1, n2)).astype(np.float32)
+    kw = dict(eps=0.02 * np.sqrt(v.size), alpha=0.4 * float(np.abs(rs["s"].astype(np.float64)).sum()),
+              beta=0.4 * float(np.abs(rs["t"].astype(np.float64)).sum()), omega=0.05)
+    with GeoSSTVSolver(n1, n2, n3, make_params(storage=storage, graph_iters=0, **kw)) as sol:
+        sol.load(torch.from_numpy(v).cuda())
+        sol.set_state({k: torch.from_numpy(rs[k]).cuda() for k in rs})
+        start = {k: x.cpu().numpy().astype(np.float64) for k, x in sol.get_state().items()}
+        sol.iterate(1)
+        got = {k: x.cpu().numpy() for k, x in sol.get_state().items()}
+    ref = o.ppds_step(o.State(**start), v.astype(np.float64), o.Params(**kw))
+    for k in got:
+        e = rel(got[k], getattr(ref, k))
+        assert e < tol, (k, e)
