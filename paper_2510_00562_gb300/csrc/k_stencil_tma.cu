@@ -1,23 +1,24 @@
-// K1, TMA-fed: the fused stencil pass of one P-PDS iteration (Algorithm 1).
+// K1, TMA-fed: the fused stencil pass of one P-PDS iteration (Algorithm 1),
+// float32 storage.
 //
 // Same arithmetic as the cooperative-load kernel in k_stencil.cu (u step and
 // u' for band b+1; w1, w2 group soft-thresholds and w' on the tile plus a
-// one-pixel ring; y1, y2 ascent for band b; window statistics of the l1
-// threshold search), fed differently: each band's planes are brought into
-// shared memory by bulk tensor (TMA) copies that one thread issues two bands
-// ahead, completing on mbarriers, so the loads of band b+2 (y, u, q, s, t,
-// y3) and b+1 (w) are in flight while band b computes.  One CTA of 512
-// threads per SM owns a 16 x 32 tile and a run of bands.  Tiles whose halo
-// stays off the image border take a specialised path with no boundary masks.
+// one-pixel ring; y1, y2 ascent; window statistics of the l1 threshold
+// search), fed differently: each band's planes are brought into shared memory
+// by bulk tensor (TMA) copies that one thread issues two bands ahead,
+// completing on mbarriers.  One CTA of 512 threads per SM owns a 16 x 32 tile
+// and a run of bands.  Tiles whose halo stays off the image border take a
+// specialised path with no boundary masks.
 //
-// The two compute phases are software-pipelined over the bands: while the w
-// steps and u' of band b run, the dual ascent and the l1 statistics of band
-// b-1 (which only read what the previous step completed) run beside them, so
-// each band costs one CTA barrier.  Shared memory per CTA (FP32): 4 slots of the
-// y-group (4 y planes with a 2-pixel halo, u and q with a 1-pixel halo
-// below/right, s, t, y3 with one row above), 3 slots of the 12 w planes
-// (1-pixel halo), u' of three bands and D^T y2 of the previous band: about
-// 211 KB.
+// Band march, one CTA barrier per band: while the w steps, u' of band b+1 and
+// the window statistics of band b run, the dual ascent of band b-1 (which
+// reads the w' and u' that the previous step completed) runs beside them.
+// Each thread keeps the four y values of its own voxel that the ascent needs
+// in registers for one band, so a y-group slot is free again as soon as its
+// band's w step is done: 3 y-group slots (y1, y2 with a 2-pixel halo, u and q
+// with a 1-pixel halo below/right, s, t, y3 with one row above) and 4 slots of
+// the 12 w planes (1-pixel halo, w' written in place) fit beside u' of three
+// bands and D^T y2 of the previous band: about 216 KB of shared memory.
 #include <algorithm>
 #include <type_traits>
 
@@ -66,57 +67,59 @@ int tma_encode_cubes(CUtensorMap* map, const void* base, int elem_bytes, int n1,
 
 namespace {
 
-template <typename T>
+constexpr int pad128(int b) { return (b + 127) / 128 * 128; }
+
 struct Lay {
     static constexpr int TY = 16, TX = 32, NT = 512;
-    static constexpr int ES = sizeof(T);
-    static constexpr int OX = 16 / ES;             // left halo columns: boxes start 16-byte aligned
+    static constexpr int OX = 4;                   // left halo columns: boxes start 16-byte aligned
     static constexpr int SW = TX + 2 * OX;         // width of the staged planes
     static constexpr int YR = TY + 4, WR = TY + 2, UR = TY + 1, UC = TX + 1;
-    static constexpr int WPC = TX + 2;             // width of the separate w' planes (16-bit storage)
-    static constexpr int pad(int b) { return (b + 127) / 128 * 128; }
-    static constexpr int Y_B = pad(YR * SW * ES);
-    static constexpr int W_B = pad(WR * SW * ES);
-    static constexpr int U_B = pad(UR * SW * ES);
-    static constexpr int S_B = pad(TY * TX * ES);
-    static constexpr int Y3_B = pad((TY + 1) * TX * ES);
+    static constexpr int Y_B = pad128(YR * SW * 4);
+    static constexpr int W_B = pad128(WR * SW * 4);
+    static constexpr int U_B = pad128(UR * SW * 4);
+    static constexpr int S_B = pad128(TY * TX * 4);
+    static constexpr int Y3_B = pad128((TY + 1) * TX * 4);
     static constexpr int YG_B = 4 * Y_B + 2 * U_B + 2 * S_B + Y3_B;
     static constexpr int WG_B = 12 * W_B;
-    static constexpr bool kInPlace = ES == 4;      // w' overwrites the staged w planes
-    static constexpr int NYS = 4, NWS = 3, NUS = 3;  // ring depths: y-group, w, u'
-    static constexpr int WP1_B = pad(12 * WR * WPC * 4);
-    static constexpr int WP_B = kInPlace ? 0 : 2 * WP1_B;
+    static constexpr int NYS = 3, NWS = 4, NUS = 3;  // ring depths: y-group, w, u'
     static constexpr int UP1 = UR * UC;              // floats of one u' plane
-    static constexpr int UP_B = pad(NUS * UP1 * 4);
-    static constexpr int G_B = pad(UR * UC * 4);
+    static constexpr int UP_B = pad128(NUS * UP1 * 4);
+    static constexpr int G_B = pad128(UR * UC * 4);
+    static constexpr int CB = 256;                   // window candidates buffered per CTA and vector
     static constexpr int OFF_WG = NYS * YG_B;
-    static constexpr int OFF_WP = OFF_WG + NWS * WG_B;
-    static constexpr int OFF_UP = OFF_WP + WP_B;
+    static constexpr int OFF_UP = OFF_WG + NWS * WG_B;
     static constexpr int OFF_G = OFF_UP + UP_B;
-    static constexpr int OFF_BAR = OFF_G + G_B;
+    static constexpr int OFF_CB = OFF_G + G_B;
+    static constexpr int OFF_BAR = OFF_CB + 2 * CB * 4;
     static constexpr int SMEM = OFF_BAR + (NYS + NWS) * 8;
-    // offsets inside a y-group slot
-    static constexpr int O_U = 4 * Y_B, O_Q = O_U + U_B, O_S = O_Q + U_B, O_T = O_S + S_B, O_Y3 = O_T + S_B;
+    // float offsets inside a y-group slot, and between planes
+    static constexpr int YPL = Y_B / 4, WPL = W_B / 4;
+    static constexpr int O_U = 4 * YPL, O_Q = O_U + U_B / 4, O_S = O_Q + U_B / 4, O_T = O_S + S_B / 4,
+                         O_Y3 = O_T + S_B / 4;
     // bytes each group's copies deliver
-    static constexpr unsigned YG_TX = 4u * YR * SW * ES + 2u * UR * SW * ES + 2u * TY * TX * ES + (TY + 1u) * TX * ES;
-    static constexpr unsigned WG_TX = 12u * WR * SW * ES;
-    static constexpr int NU = TY * TX + (TX + 1) + TY;
-    static constexpr int NW = TY * TX + 2 * (TX + 2) + 2 * TY;
+    static constexpr unsigned YG_TX = 4u * YR * SW * 4 + 2u * UR * SW * 4 + 2u * TY * TX * 4 + (TY + 1u) * TX * 4;
+    static constexpr unsigned WG_TX = 12u * WR * SW * 4;
+    // one-pixel ring: w positions 2 (TX + 2) + 2 TY per set, u' positions (TX + 1) + TY
+    static constexpr int NWR = 2 * (TX + 2) + 2 * TY, NUR = (TX + 1) + TY;
     static_assert(TY * TX == NT, "one tile voxel per thread");
-    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(SMEM + 1200 <= 227 * 1024, "shared memory");
+    static_assert(2 * NWR <= 224 && NUR <= 32 + 32, "ring work layout");
 };
 
-template <typename T>
 struct K1TArgs {
     Geom g;
-    T *u_n, *w1_n, *w2_n, *y1_n, *y2_n;
+    float *u_n, *w1_n, *w2_n, *y1_n, *y2_n;
     IterParams p;
     Scal* sc;
     L1Work l1;
     int chunk;
 };
 
-template <typename T> __device__ __forceinline__ float sld(const T* p) { return ldT(p); }
+// Window of the l1 threshold search for this launch (see gsstv_l1.cuh).
+struct K1Win {
+    bool s, t;
+    float lo_s, hi_s, lo_t, hi_t;
+};
 
 // Per-CTA running state shared by the two tile paths.
 struct K1State {
@@ -124,59 +127,121 @@ struct K1State {
     unsigned n_y = 0, n_w = 0;   // groups issued so far (thread 0 only)
 };
 
-template <typename T, bool EDGE>
-__device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, unsigned char* sm, int i0,
-                                        int j0, int b0, int b1, K1State& S, bool win_s, bool win_t,
-                                        float lo_s, float hi_s, float lo_t, float hi_t, float cs) {
-    using L = Lay<T>;
+// Appends the lanes' window candidates to the CTA's shared buffer (one
+// shared-memory atomic per warp); values past its end go straight to the
+// global list.  `cnt` keeps counting past the buffer.
+__device__ __forceinline__ void append_shared(bool take, float x, float* buf, unsigned* cnt, float* cand,
+                                              unsigned* gcnt) {
+    const unsigned mask = __ballot_sync(0xffffffffu, take);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const unsigned k = base + __popc(mask & ((1u << lane) - 1u));
+    if (take && k < (unsigned)Lay::CB) buf[k] = x;
+    if (base + __popc(mask) > (unsigned)Lay::CB) append_candidate(take && k >= (unsigned)Lay::CB, x, cand, gcnt);
+}
+
+// Sum over the CTA of the threads' compensated sums, carried as unevaluated
+// float pairs (hi + lo, Knuth's two-sum at every step) so that no FP64
+// instruction runs per warp; the pair becomes a double on thread 0 only.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float bhi, float blo) {
+    float s, e;
+    two_sum(hi, bhi, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, blo));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+__device__ double block_sum_pair(const Kahan& k, float2* buf) {
+    float hi = k.s, lo = -k.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
+        pair_add(hi, lo, bh, bl);
+    }
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) buf[w] = make_float2(hi, lo);
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        float h = buf[0].x, l = buf[0].y;
+        for (int k2 = 1; k2 < nw; ++k2) pair_add(h, l, buf[k2].x, buf[k2].y);
+        r = (double)h + (double)l;
+    }
+    return r;
+}
+
+// Counts x into a window accumulator when `take`, without a branch.
+__device__ __forceinline__ void win_add(WinAcc& A, bool take, float x) {
+    Kahan k = A.s;
+    k.add(x);
+    A.n += take ? 1ull : 0ull;
+    A.s.s = take ? k.s : A.s.s;
+    A.s.c = take ? k.c : A.s.c;
+}
+
+// value of a set selector: an int, or a std::integral_constant
+template <typename X> __device__ __forceinline__ constexpr int set_of(X x) {
+    if constexpr (std::is_integral<X>::value) return x;
+    else return X::value;
+}
+
+using Set0 = std::integral_constant<int, 0>;
+using Set1 = std::integral_constant<int, 1>;
+using Store = std::true_type;
+using NoStore = std::false_type;
+
+template <bool EDGE>
+__device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsigned char* sm, unsigned* ccnt,
+                                        int i0, int j0, int b0, int b1, K1State& S, const K1Win& W, float cs) {
+    using L = Lay;
     constexpr int TY = L::TY, TX = L::TX, SW = L::SW, OX = L::OX, UC = L::UC;
-    constexpr int WP_ROW = L::kInPlace ? SW : L::WPC;
+    constexpr int YPL = L::YPL, WPL = L::WPL;
     const Geom& g = a.g;
     const IterParams& P = a.p;
     const int tid = threadIdx.x;
-    const unsigned cube = (unsigned)g.cube;        // < 2^31 (checked at handle creation)
+    const unsigned cube = (unsigned)g.cube;        // 6 cubes < 2^32 elements (checked at handle creation)
     const unsigned plane = (unsigned)g.n1 * (unsigned)g.p2;
     uint64_t* ybar = reinterpret_cast<uint64_t*>(sm + L::OFF_BAR);
     uint64_t* wbar = ybar + L::NYS;
     float* up = reinterpret_cast<float*>(sm + L::OFF_UP);
     float* gs = reinterpret_cast<float*>(sm + L::OFF_G);
+    float* cbuf = reinterpret_cast<float*>(sm + L::OFF_CB);
     const int bstart = max(b0 - 1, 0);
     const int blast = min(b1, g.n3 - 1);
-    const unsigned it32 = (unsigned)a.sc->iter;     // seeds the 16-bit rounding streams
 
-    // ---- ring slots (computed once per band by the callers below) ----
-    auto yg = [&](int band) { return sm + ((band - bstart) % L::NYS) * L::YG_B; };
-    auto wg = [&](int band) { return sm + L::OFF_WG + ((band - b0) % L::NWS) * L::WG_B; };
-    // w' of a band: in place in its w slot (FP32), else in one of two float
-    // planes that alternate with the band (16-bit storage)
-    auto wpl = [&](int band) -> float* {
-        if constexpr (L::kInPlace) return reinterpret_cast<float*>(wg(band));
-        else return reinterpret_cast<float*>(sm + L::OFF_WP + ((band - b0) & 1) * L::WP1_B);
-    };
-    constexpr int WP_PL = L::kInPlace ? L::W_B / 4 : L::WR * L::WPC;   // floats between w' planes
+    // ---- ring slots ----
+    auto ygb = [&](int band) { return sm + ((band - bstart) % L::NYS) * L::YG_B; };
+    auto wgb = [&](int band) { return sm + L::OFF_WG + ((band - b0) % L::NWS) * L::WG_B; };
+    auto yg = [&](int band) { return reinterpret_cast<const float*>(ygb(band)); };
+    auto wg = [&](int band) { return reinterpret_cast<float*>(wgb(band)); };
     auto upl = [&](int band) { return up + (band % L::NUS) * L::UP1; };
-    auto wp_idx = [&](int r, int c) {
-        if constexpr (L::kInPlace) return (r + 1) * SW + (c + OX);
-        else return (r + 1) * L::WPC + (c + 1);
-    };
 
     auto issue_y = [&](int band) {
-        unsigned char* s = yg(band);
+        unsigned char* s = ygb(band);
         uint64_t* bar = ybar + (band - bstart) % L::NYS;
         mbar_arrive_expect_tx(bar, L::YG_TX);
         tma_load_3d(s + 0 * L::Y_B, &M.y1, j0 - OX, i0 - 2, band, bar);
         tma_load_3d(s + 1 * L::Y_B, &M.y1, j0 - OX, i0 - 2, g.n3 + band, bar);
         tma_load_3d(s + 2 * L::Y_B, &M.y2, j0 - OX, i0 - 2, band, bar);
         tma_load_3d(s + 3 * L::Y_B, &M.y2, j0 - OX, i0 - 2, g.n3 + band, bar);
-        tma_load_3d(s + L::O_U, &M.u, j0 - OX, i0, band, bar);
-        tma_load_3d(s + L::O_Q, &M.q, j0 - OX, i0, band, bar);
-        tma_load_3d(s + L::O_S, &M.s, j0, i0, band, bar);
-        tma_load_3d(s + L::O_T, &M.t, j0, i0, band, bar);
-        tma_load_3d(s + L::O_Y3, &M.y3, j0, i0 - 1, band, bar);
+        tma_load_3d(s + 4 * L::O_U, &M.u, j0 - OX, i0, band, bar);
+        tma_load_3d(s + 4 * L::O_Q, &M.q, j0 - OX, i0, band, bar);
+        tma_load_3d(s + 4 * L::O_S, &M.s, j0, i0, band, bar);
+        tma_load_3d(s + 4 * L::O_T, &M.t, j0, i0, band, bar);
+        tma_load_3d(s + 4 * L::O_Y3, &M.y3, j0, i0 - 1, band, bar);
         S.n_y++;
     };
     auto issue_w = [&](int band) {
-        unsigned char* s = wg(band);
+        unsigned char* s = wgb(band);
         uint64_t* bar = wbar + (band - b0) % L::NWS;
         mbar_arrive_expect_tx(bar, L::WG_TX);
         for (int k = 0; k < 6; ++k) tma_load_3d(s + k * L::W_B, &M.w1, j0 - OX, i0 - 1, k * g.n3 + band, bar);
@@ -189,70 +254,68 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
     auto wait_w = [&](int band) { return mbar_wait(wbar + (band - b0) % L::NWS, ((band - b0) / L::NWS) & 1); };
 
     // D^T y = D_v^T y_v + D_h^T y_h at tile-relative (r, c); yv, yh: y planes
-    auto dty = [&](const T* yv, const T* yh, int r, int c) {
+    auto dty = [&](const float* yv, const float* yh, int r, int c) {
         const int k = (r + 2) * SW + (c + OX);
         if constexpr (EDGE) {
             const int gi = i0 + r, gj = j0 + c;
             float d = 0.f;
-            if (gi >= 1) d += sld(yv + k - SW);
-            if (gi <= g.n1 - 2) d -= sld(yv + k);
-            if (gj >= 1) d += sld(yh + k - 1);
-            if (gj <= g.n2 - 2) d -= sld(yh + k);
+            if (gi >= 1) d += yv[k - SW];
+            if (gi <= g.n1 - 2) d -= yv[k];
+            if (gj >= 1) d += yh[k - 1];
+            if (gj <= g.n2 - 2) d -= yh[k];
             return d;
         } else {
-            return ((sld(yv + k - SW) - sld(yv + k)) + sld(yh + k - 1)) - sld(yh + k);
+            return ((yv[k - SW] - yv[k]) + yh[k - 1]) - yh[k];
         }
     };
     // u step and u' of band bb at (r, c) in [0, TY] x [0, TX]; ys: y-group of
-    // bb; upb: u' plane of bb; dst: u+ of this voxel, or null (no store)
-    auto u_item = [&](const unsigned char* ys, float* upb, int bb, int r, int c, T* dst) {
+    // bb; upb: u' plane of bb; with Store, u+ goes to *dst when `st`
+    auto u_item = [&](auto store_c, const float* ys, float* upb, int bb, int r, int c, float* dst, bool st) {
         const int kc = r * UC + c;
         if constexpr (EDGE) {
             if (i0 + r >= g.n1 || j0 + c >= g.n2) { upb[kc] = 0.f; gs[kc] = 0.f; return; }
         }
-        const T* yp = reinterpret_cast<const T*>(ys);
-        const float d1 = dty(yp, yp + L::Y_B / L::ES, r, c);
-        const float gcur = dty(yp + 2 * (L::Y_B / L::ES), yp + 3 * (L::Y_B / L::ES), r, c);
+        const float d1 = dty(ys, ys + YPL, r, c);
+        const float gcur = dty(ys + 2 * YPL, ys + 3 * YPL, r, c);
+        const float gprev = gs[kc];
         float dst_ = 0.f;
-        if (bb >= 1) dst_ += gs[kc];
+        if (bb >= 1) dst_ += gprev;
         if (bb <= g.n3 - 2) dst_ -= gcur;
         const int ku = r * SW + (c + OX);
-        const float y4 = cs * sld(reinterpret_cast<const T*>(ys + L::O_Q) + ku);
-        const float u = sld(reinterpret_cast<const T*>(ys + L::O_U) + ku);
+        const float y4 = cs * ys[L::O_Q + ku];
+        const float u = ys[L::O_U + ku];
         const float un = fminf(fmaxf(u - P.gamma_u * (d1 + dst_ + y4), P.mu_lo), P.mu_hi);
         upb[kc] = 2.f * un - u;
         gs[kc] = gcur;
-        if (dst) {
-            SRStream sr((unsigned)(dst - a.u_n), it32, 2u);
-            stS(dst, un, sr);
+        if constexpr (decltype(store_c)::value) {
+            if (st) *dst = un;
         }
     };
-    // w step of one set (a compile-time constant: 0 = w1, 1 = w2) at (r, c)
-    // in [-1, TY] x [-1, TX]; ys: y-group, wst: staged w planes, wp: w' planes
-    // of the band; dst: w+ of this voxel (set's first plane), or null on the ring
-    auto w_item = [&](auto set_c, const unsigned char* ys, const T* wst, float* wp, int r, int c, T* dst) {
-        constexpr int set = decltype(set_c)::value;
+    // w step of one set (0 = w1, 1 = w2; a compile-time constant or not) at
+    // (r, c) in [-1, TY] x [-1, TX]; w' overwrites w in place; with Store, w+
+    // goes to dst (the set's first plane) when `st`
+    auto w_item = [&](auto set_c, auto store_c, const float* ys, float* wst, int r, int c, float* dst, bool st) {
+        const int set = set_of(set_c);
         const int kw = (r + 1) * SW + (c + OX);
-        const int kp = wp_idx(r, c);
         const int gi = i0 + r, gj = j0 + c;
         if constexpr (EDGE) {
             if (gi < 0 || gi >= g.n1 || gj < 0 || gj >= g.n2) {
 #pragma unroll
-                for (int k = 6 * set; k < 6 * set + 6; ++k) wp[k * WP_PL + kp] = 0.f;
+                for (int k = 0; k < 6; ++k) wst[(6 * set + k) * WPL + kw] = 0.f;
                 return;
             }
         }
         const bool mv = !EDGE || gi < g.n1 - 1, mh = !EDGE || gj < g.n2 - 1;
         const int ky = (r + 2) * SW + (c + OX);
-        const T* yv = reinterpret_cast<const T*>(ys + (2 * set) * L::Y_B) + ky;
-        const T* yh = reinterpret_cast<const T*>(ys + (2 * set + 1) * L::Y_B) + ky;
+        const float* yv = ys + (2 * set) * YPL + ky;
+        const float* yh = yv + YPL;
         auto V = [&](int dr, int dc) {
-            if constexpr (EDGE) return (gi + dr == g.n1 - 1) ? 0.f : sld(yv + dr * SW + dc);
-            else return sld(yv + dr * SW + dc);
+            if constexpr (EDGE) return (gi + dr == g.n1 - 1) ? 0.f : yv[dr * SW + dc];
+            else return yv[dr * SW + dc];
         };
         auto H = [&](int dr, int dc) {
-            if constexpr (EDGE) return (gj + dc == g.n2 - 1) ? 0.f : sld(yh + dr * SW + dc);
-            else return sld(yh + dr * SW + dc);
+            if constexpr (EDGE) return (gj + dc == g.n2 - 1) ? 0.f : yh[dr * SW + dc];
+            else return yh[dr * SW + dc];
         };
         const float v00 = V(0, 0), vm0 = V(-1, 0), v01 = V(0, 1), vm1 = V(-1, 1);
         const float h00 = H(0, 0), h0m = H(0, -1), h10 = H(1, 0), h1m = H(1, -1);
@@ -266,200 +329,191 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs<T>& a, un
         const float gam = set ? P.gamma_w2 : P.gamma_w1;
         const float thr = set ? P.thr_w2 : P.thr_w1;
         const float thr2 = thr * thr;
-        SRStream sr(dst ? (unsigned)(dst - (set ? a.w2_n : a.w1_n)) : 0u, it32, 4u + set);
+        float* wp = wst + (6 * set) * WPL + kw;
 #pragma unroll
         for (int gr = 0; gr < 3; ++gr) {
-            const int kv = 6 * set + 2 * gr;
-            const float wv = sld(wst + kv * (L::W_B / L::ES) + kw);
-            const float wh = sld(wst + (kv + 1) * (L::W_B / L::ES) + kw);
+            const float wv = wp[(2 * gr) * WPL];
+            const float wh = wp[(2 * gr + 1) * WPL];
             const float xv = wv + gam * Lv[gr], xh = wh + gam * Lh[gr];
             // Eq. 24: max(1 - thr / ||x||, 0) x, with 1 / ||x|| from rsqrt
             const float n2 = xv * xv + xh * xh;
             const float sc = n2 > thr2 ? fmaxf(1.f - thr * rsqrtf(n2), 0.f) : 0.f;
             const float nv = sc * xv, nh = sc * xh;
-            wp[kv * WP_PL + kp] = 2.f * nv - wv;
-            wp[(kv + 1) * WP_PL + kp] = 2.f * nh - wh;
-            if (dst) {
-                stS(dst + (2 * gr) * cube, nv, sr);
-                stS(dst + (2 * gr + 1) * cube, nh, sr);
+            wp[(2 * gr) * WPL] = 2.f * nv - wv;
+            wp[(2 * gr + 1) * WPL] = 2.f * nh - wh;
+            if constexpr (decltype(store_c)::value) {
+                if (st) {
+                    dst[(2 * gr) * cube] = nv;
+                    dst[(2 * gr + 1) * cube] = nh;
+                }
             }
         }
     };
-    using Set0 = std::integral_constant<int, 0>;
-    using Set1 = std::integral_constant<int, 1>;
 
     // ---- this thread's tile voxel and its share of the one-pixel ring ----
     const int r_t = tid / TX, c_t = tid - (tid / TX) * TX;
     const int gi_t = i0 + r_t, gj_t = j0 + c_t;
     const bool valid_t = !EDGE || (gi_t < g.n1 && gj_t < g.n2);
     const unsigned o_t = valid_t ? (unsigned)gi_t * (unsigned)g.p2 + (unsigned)gj_t : 0u;
-    // ring w positions: 2 (TX + 2) + 2 TY; each set takes four warps (128
-    // threads, one position each) so a warp never mixes the two sets; ring u'
-    // positions ((TX + 1) + TY) go to the next warps
-    constexpr int NWR = 2 * (TX + 2) + 2 * TY;
-    constexpr int NUR = (TX + 1) + TY;
-    static_assert(NWR <= 128 && 256 + NUR <= L::NT, "ring work layout");
+    const int ky_t = (r_t + 2) * SW + (c_t + OX);
+    // Ring w items (both sets, set 0 first) on threads 0..2 NWR-1 (warps 0-6),
+    // ring u' items on warps 7 and 11: each scheduler (warp index mod 4) gets
+    // at most two ring warps besides its four tile warps.
     int rw_r = 0, rw_c = 0, ru_r = 0, ru_c = 0;
-    const int rw_set = tid >> 7;                       // 0 or 1 for tid < 256
-    const bool has_rw = tid < 256 && (tid & 127) < NWR;
-    const bool has_ru = tid >= 256 && tid < 256 + NUR;
+    const bool has_rw = tid < 2 * L::NWR;
+    const int rw_set = tid >= L::NWR ? 1 : 0;
+    const int ru_k = tid >= 224 && tid < 256 ? tid - 224 : tid >= 352 && tid < 384 ? tid - 352 + 32 : L::NUR;
+    const bool has_ru = ru_k < L::NUR;
     if (has_rw) {
-        int k = tid & 127;
+        int k = tid - rw_set * L::NWR;
         if (k < TX + 2) { rw_r = -1; rw_c = k - 1; }
         else if ((k -= TX + 2) < TX + 2) { rw_r = TY; rw_c = k - 1; }
         else if ((k -= TX + 2) < TY) { rw_r = k; rw_c = -1; }
         else { rw_r = k - TY; rw_c = TX; }
     }
     if (has_ru) {
-        const int k = tid - 256;
-        if (k < TX + 1) { ru_r = TY; ru_c = k; } else { ru_r = k - (TX + 1); ru_c = TX; }
+        if (ru_k < TX + 1) { ru_r = TY; ru_c = ru_k; } else { ru_r = ru_k - (TX + 1); ru_c = TX; }
     }
 
-    // ---- dual ascent of y1, y2 and the l1 window statistics of one band ----
-    // Reads the band's completed w', u' of the band and the next, its y-group.
-    auto t_item = [&](int band) {
-        const bool nxt = band + 1 < g.n3;
-        const float* upb = upl(band);
-        const float* upn = upl(band + 1);
-        const unsigned char* ys = yg(band);
-        const float* wp = wpl(band);
-        const unsigned ob = (unsigned)band * plane + o_t;
+    // ---- dual ascent of y1, y2 at this thread's voxel of band tb ----
+    // Reads the band's completed w' and u' of the band and the next; yc: the
+    // voxel's y1 (v, h), y2 (v, h) of band tb.
+    auto t_item = [&](int tb, const float (&yc)[4]) {
+        if (!valid_t) return;
+        const bool nxt = tb + 1 < g.n3;
+        const float* upb = upl(tb);
+        const float* upn = upl(tb + 1);
+        const float* wp = wg(tb);
+        const int kc = r_t * UC + c_t;
+        const float u0 = upb[kc];
+        const bool mv = !EDGE || gi_t < g.n1 - 1, mh = !EDGE || gj_t < g.n2 - 1;
+        const float duv = mv ? upb[kc + UC] - u0 : 0.f;
+        const float duh = mh ? upb[kc + 1] - u0 : 0.f;
+        const float d0 = upn[kc] - u0;
+        const float ddv = nxt && mv ? (upn[kc + UC] - upb[kc + UC]) - d0 : 0.f;
+        const float ddh = nxt && mh ? (upn[kc + 1] - upb[kc + 1]) - d0 : 0.f;
+        const float* wk = wp + (r_t + 1) * SW + (c_t + OX);
+        float gv[2], gh[2];
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+            auto Wk = [&](int k, int dr, int dc) { return wk[(6 * set + k) * WPL + dr * SW + dc]; };
+            auto A_ = [&](int dr, int dc) {
+                if constexpr (EDGE) return (gi_t + dr < g.n1 - 1) ? Wk(1, dr, dc) : 0.f;
+                else return Wk(1, dr, dc);
+            };
+            auto B_ = [&](int dr, int dc) {
+                if constexpr (EDGE) return (gj_t + dc < g.n2 - 1) ? Wk(2, dr, dc) : 0.f;
+                else return Wk(2, dr, dc);
+            };
+            gv[set] = mv ? (Wk(0, 0, 0) + 0.25f * (B_(0, 0) + B_(1, 0) + B_(0, -1) + B_(1, -1))
+                            + 0.5f * (Wk(4, 0, 0) + Wk(4, 1, 0)))
+                         : 0.f;
+            gh[set] = mh ? (0.25f * (A_(0, 0) + A_(0, 1) + A_(-1, 0) + A_(-1, 1)) + Wk(3, 0, 0)
+                            + 0.5f * (Wk(5, 0, 0) + Wk(5, 0, 1)))
+                         : 0.f;
+        }
+        const unsigned ob = (unsigned)tb * plane + o_t;
+        a.y1_n[ob] = yc[0] + P.gamma_y1 * (duv - gv[0]);
+        a.y1_n[cube + ob] = yc[1] + P.gamma_y1 * (duh - gh[0]);
+        a.y2_n[ob] = yc[2] + P.gamma_y2 * (ddv - gv[1]);
+        a.y2_n[cube + ob] = yc[3] + P.gamma_y2 * (ddh - gh[1]);
+    };
+
+    // ---- l1 window statistics of s~, t~ at this thread's voxel ----
+    auto stats = [&](const float* ys) {
         float xs = 0.f, xt = 0.f;
         if (valid_t) {
-            const int r = r_t, c = c_t;
-            const int kc = r * UC + c;
-            const float u0 = upb[kc];
-            const bool mv = !EDGE || gi_t < g.n1 - 1, mh = !EDGE || gj_t < g.n2 - 1;
-            const float duv = mv ? upb[kc + UC] - u0 : 0.f;
-            const float duh = mh ? upb[kc + 1] - u0 : 0.f;
-            float ddv = 0.f, ddh = 0.f;
-            if (nxt) {
-                const float d0 = upn[kc] - u0;
-                if (mv) ddv = (upn[kc + UC] - upb[kc + UC]) - d0;
-                if (mh) ddh = (upn[kc + 1] - upb[kc + 1]) - d0;
-            }
-            const float* wk = wp + wp_idx(r, c);
-            float gv[2], gh[2];
-#pragma unroll
-            for (int set = 0; set < 2; ++set) {
-                auto Wk = [&](int k, int dr, int dc) { return wk[(6 * set + k) * WP_PL + dr * WP_ROW + dc]; };
-                auto A_ = [&](int dr, int dc) {
-                    if constexpr (EDGE) return (gi_t + dr < g.n1 - 1) ? Wk(1, dr, dc) : 0.f;
-                    else return Wk(1, dr, dc);
-                };
-                auto B_ = [&](int dr, int dc) {
-                    if constexpr (EDGE) return (gj_t + dc < g.n2 - 1) ? Wk(2, dr, dc) : 0.f;
-                    else return Wk(2, dr, dc);
-                };
-                gv[set] = mv ? (Wk(0, 0, 0) + 0.25f * (B_(0, 0) + B_(1, 0) + B_(0, -1) + B_(1, -1))
-                                + 0.5f * (Wk(4, 0, 0) + Wk(4, 1, 0)))
-                             : 0.f;
-                gh[set] = mh ? (0.25f * (A_(0, 0) + A_(0, 1) + A_(-1, 0) + A_(-1, 1)) + Wk(3, 0, 0)
-                                + 0.5f * (Wk(5, 0, 0) + Wk(5, 0, 1)))
-                             : 0.f;
-            }
-            const int ky = (r + 2) * SW + (c + OX);
-            const T* yp = reinterpret_cast<const T*>(ys) + ky;
-            constexpr int YPL = L::Y_B / L::ES;
-            SRStream sr(ob, it32, 3u);
-            stS(a.y1_n + ob, sld(yp) + P.gamma_y1 * (duv - gv[0]), sr);
-            stS(a.y1_n + cube + ob, sld(yp + YPL) + P.gamma_y1 * (duh - gh[0]), sr);
-            stS(a.y2_n + ob, sld(yp + 2 * YPL) + P.gamma_y2 * (ddv - gv[1]), sr);
-            stS(a.y2_n + cube + ob, sld(yp + 3 * YPL) + P.gamma_y2 * (ddh - gh[1]), sr);
-            if (win_s || win_t) {
-                const T* q = reinterpret_cast<const T*>(ys + L::O_Q);
-                const T* sp = reinterpret_cast<const T*>(ys + L::O_S);
-                const T* tp = reinterpret_cast<const T*>(ys + L::O_T);
-                const T* y3p = reinterpret_cast<const T*>(ys + L::O_Y3);
-                const float qv = sld(q + r * SW + (c + OX));
-                const float y3v = sld(y3p + (r + 1) * TX + c);
-                const float y3u = (!EDGE || gi_t >= 1) ? sld(y3p + r * TX + c) : 0.f;
-                s_t_tilde(sld(sp + r * TX + c), sld(tp + r * TX + c), y3v, y3u, qv, cs, gi_t, g.n1,
-                          P.gamma_s, P.gamma_t, xs, xt);
-            }
+            const float qv = ys[L::O_Q + r_t * SW + (c_t + OX)];
+            const float y3v = ys[L::O_Y3 + (r_t + 1) * TX + c_t];
+            const float y3u = (!EDGE || gi_t >= 1) ? ys[L::O_Y3 + r_t * TX + c_t] : 0.f;
+            s_t_tilde(ys[L::O_S + r_t * TX + c_t], ys[L::O_T + r_t * TX + c_t], y3v, y3u, qv, cs, gi_t, g.n1,
+                      P.gamma_s, P.gamma_t, xs, xt);
         }
-        if (win_s) {
-            const float x = fabsf(xs);
-            const bool hi = valid_t && x > hi_s;
-            if (hi) { S.acc_s.n++; S.acc_s.s.add(x); }
-            append_candidate(valid_t && !hi && x > lo_s, x, a.l1.cand[0], &a.sc->acc[0].m);
-        }
-        if (win_t) {
-            const float x = fabsf(xt);
-            const bool hi = valid_t && x > hi_t;
-            if (hi) { S.acc_t.n++; S.acc_t.s.add(x); }
-            append_candidate(valid_t && !hi && x > lo_t, x, a.l1.cand[1], &a.sc->acc[1].m);
-        }
+        // an inactive window has lo = hi = +inf: nothing is counted or taken
+        const float x_s = fabsf(xs), x_t = fabsf(xt);
+        const bool hs = valid_t && x_s > W.hi_s, ht = valid_t && x_t > W.hi_t;
+        win_add(S.acc_s, hs, x_s);
+        win_add(S.acc_t, ht, x_t);
+        append_shared(valid_t && !hs && x_s > W.lo_s, x_s, cbuf, ccnt, a.l1.cand[0], &a.sc->acc[0].m);
+        append_shared(valid_t && !ht && x_t > W.lo_t, x_t, cbuf + L::CB, ccnt + 1, a.l1.cand[1], &a.sc->acc[1].m);
     };
 
     // ---- prologue: D^T y2 of band b0-1 and u' of band b0 ----
     if (tid == 0) {
-        for (int band = bstart; band <= min(bstart + 2, blast); ++band) issue_y(band);
+        for (int band = bstart; band <= min(bstart + L::NYS - 1, blast); ++band) issue_y(band);
         issue_w(b0);
+        if (b0 + 1 < b1) issue_w(b0 + 1);
     }
     bool ok = true;
     if (b0 >= 1) {
         ok = wait_y(b0 - 1);
-        const T* yp = reinterpret_cast<const T*>(yg(b0 - 1));
+        const float* yp = yg(b0 - 1);
         for (int e = tid; e < L::UR * UC; e += L::NT) {
             const int r = e / UC, c = e - r * UC;
             if (EDGE && (i0 + r >= g.n1 || j0 + c >= g.n2)) { gs[e] = 0.f; continue; }
-            gs[e] = dty(yp + 2 * (L::Y_B / L::ES), yp + 3 * (L::Y_B / L::ES), r, c);
+            gs[e] = dty(yp + 2 * YPL, yp + 3 * YPL, r, c);
         }
     }
     ok = wait_y(b0) && ok;
     ok = __syncthreads_and(ok);
     if (!ok) return false;
-    {
-        const unsigned char* ys0 = yg(b0);
-        float* up0 = upl(b0);
-        u_item(ys0, up0, b0, r_t, c_t, valid_t ? a.u_n + ((unsigned)b0 * plane + o_t) : nullptr);
-        if (has_ru) u_item(ys0, up0, b0, ru_r, ru_c, nullptr);
-    }
+    u_item(Store{}, yg(b0), upl(b0), b0, r_t, c_t, a.u_n + ((unsigned)b0 * plane + o_t), valid_t);
+    if (has_ru) u_item(NoStore{}, yg(b0), upl(b0), b0, ru_r, ru_c, nullptr, false);
     __syncthreads();
 
-    // ---- band march, one barrier per band: w steps and u' of band b beside
-    // the dual ascent of band b-1 ----
-    for (int b = b0; b < b1; ++b) {
+    // ---- band march, one barrier per band ----
+    // The tile work of a band is one straight run (w steps, the ascent of the
+    // previous band, u' of the next, the statistics) so that the compiler can
+    // interleave their independent chains; the ring work follows.  u' of the
+    // band past the cube's last one is computed from a stale slot and not
+    // stored (its values are never used).
+    float yprev[4] = {0.f, 0.f, 0.f, 0.f};
+    auto step = [&](int b, auto do_t) -> bool {
         const bool has_next = b + 1 < g.n3;
         if (tid == 0) {
-            if (b + 2 <= blast && (b + 2 - bstart) >= 3) issue_y(b + 2);
-            if (b + 1 < b1) issue_w(b + 1);
+            if (b + 2 <= blast && b + 2 - bstart >= L::NYS) issue_y(b + 2);
+            if (b + 2 < b1) issue_w(b + 2);
         }
         bool okb = wait_w(b);
         if (has_next) okb = wait_y(b + 1) && okb;
+        okb = __all_sync(0xffffffffu, okb);   // warp-uniform: the statistics use warp votes
         if (okb) {
-            const unsigned char* ys = yg(b);
-            const unsigned char* ysn = yg(b + 1);
-            const T* wst = reinterpret_cast<const T*>(wg(b));
-            float* wp = wpl(b);
+            const float* ys = yg(b);
+            const float* ysn = yg(b + 1);
+            float* wst = wg(b);
             float* upn = upl(b + 1);
             const unsigned ob = (unsigned)b * plane + o_t;
-            w_item(Set0{}, ys, wst, wp, r_t, c_t, valid_t ? a.w1_n + ob : nullptr);
-            w_item(Set1{}, ys, wst, wp, r_t, c_t, valid_t ? a.w2_n + ob : nullptr);
-            if (has_next) u_item(ysn, upn, b + 1, r_t, c_t, (valid_t && b + 1 < b1) ? a.u_n + (ob + plane) : nullptr);
-            if (has_rw) {
-                if (rw_set == 0) w_item(Set0{}, ys, wst, wp, rw_r, rw_c, nullptr);
-                else w_item(Set1{}, ys, wst, wp, rw_r, rw_c, nullptr);
-            }
-            if (has_ru && has_next) u_item(ysn, upn, b + 1, ru_r, ru_c, nullptr);
+            float ycur[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ycur[k] = ys[k * YPL + ky_t];
+            w_item(Set0{}, Store{}, ys, wst, r_t, c_t, a.w1_n + ob, valid_t);
+            w_item(Set1{}, Store{}, ys, wst, r_t, c_t, a.w2_n + ob, valid_t);
+            if constexpr (decltype(do_t)::value) t_item(b - 1, yprev);
+            u_item(Store{}, ysn, upn, b + 1, r_t, c_t, a.u_n + (ob + plane), valid_t && b + 1 < b1);
+            if (W.s || W.t) stats(ys);
+            if (has_rw) w_item(rw_set, NoStore{}, ys, wst, rw_r, rw_c, nullptr, false);
+            if (has_ru && has_next) u_item(NoStore{}, ysn, upn, b + 1, ru_r, ru_c, nullptr, false);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) yprev[k] = ycur[k];
         }
-        if (b > b0) t_item(b - 1);
         // the slots freed at this step are reloaded by TMA at the next one:
         // order this thread's generic accesses before those async-proxy writes
         fence_proxy_async_smem();
-        if (__syncthreads_or(!okb)) return false;
-    }
-    t_item(b1 - 1);
+        return !__syncthreads_or(!okb);
+    };
+    if (!step(b0, std::false_type{})) return false;
+    for (int b = b0 + 1; b < b1; ++b)
+        if (!step(b, std::true_type{})) return false;
+    t_item(b1 - 1, yprev);
     return true;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps maps, const K1TArgs<T> a) {
-    using L = Lay<T>;
+__global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps maps, const K1TArgs a) {
+    using L = Lay;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ double red_d[64];
     __shared__ unsigned long long red_u[64];
+    __shared__ unsigned ccnt[2], cbase[2];
     __shared__ int is_last;
     const Geom& g = a.g;
     const IterParams& P = a.p;
@@ -468,22 +522,24 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     const int b1 = min(g.n3, b0 + a.chunk);
     const int tid = threadIdx.x;
     const float cs = (float)(1.0 - a.sc->c[P.parity]);
-    const bool win_s = !P.tau_exact && a.sc->radius[0] > 0.0 && a.sc->ctl[0].window_ok;
-    const bool win_t = !P.tau_exact && a.sc->radius[1] > 0.0 && a.sc->ctl[1].window_ok;
-    const float lo_s = a.sc->ctl[0].theta_lo, hi_s = a.sc->ctl[0].theta_hi;
-    const float lo_t = a.sc->ctl[1].theta_lo, hi_t = a.sc->ctl[1].theta_hi;
+    K1Win W;
+    W.s = !P.tau_exact && a.sc->radius[0] > 0.0 && a.sc->ctl[0].window_ok;
+    W.t = !P.tau_exact && a.sc->radius[1] > 0.0 && a.sc->ctl[1].window_ok;
+    W.lo_s = W.s ? a.sc->ctl[0].theta_lo : INFINITY; W.hi_s = W.s ? a.sc->ctl[0].theta_hi : INFINITY;
+    W.lo_t = W.t ? a.sc->ctl[1].theta_lo : INFINITY; W.hi_t = W.t ? a.sc->ctl[1].theta_hi : INFINITY;
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::OFF_BAR);
     if (tid == 0) {
         for (int k = 0; k < L::NYS + L::NWS; ++k) mbar_init(bars + k, 1);
         mbar_fence_init();
+        ccnt[0] = ccnt[1] = 0;
     }
     __syncthreads();
 
     K1State S;
     const bool edge = !(i0 >= 2 && i0 + L::TY + 3 <= g.n1 && j0 >= 2 && j0 + L::TX + 3 <= g.n2);
-    bool ok = edge ? k1_tile<T, true>(maps, a, sm, i0, j0, b0, b1, S, win_s, win_t, lo_s, hi_s, lo_t, hi_t, cs)
-                   : k1_tile<T, false>(maps, a, sm, i0, j0, b0, b1, S, win_s, win_t, lo_s, hi_s, lo_t, hi_t, cs);
+    const bool ok = edge ? k1_tile<true>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs)
+                         : k1_tile<false>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs);
     if (!ok) {
         // a load never arrived: record it, let this CTA's copies land (bounded)
         // before its shared memory is released, and skip the statistics
@@ -500,11 +556,25 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
 
     const int cta = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int ncta = gridDim.x * gridDim.y * gridDim.z;
-    if (win_s || win_t) {
+    if (W.s || W.t) {
+        // the buffered window candidates join the global list (one atomic per vector)
+        __syncthreads();
+        if (tid < 2) {
+            const unsigned n = min(ccnt[tid], (unsigned)L::CB);
+            cbase[tid] = n ? atomicAdd(&a.sc->acc[tid].m, n) : 0u;
+        }
+        __syncthreads();
+        const float* cbuf = reinterpret_cast<const float*>(sm + L::OFF_CB);
+        for (int v = 0; v < 2; ++v) {
+            const unsigned n = min(ccnt[v], (unsigned)L::CB);
+            for (unsigned k = tid; k < n; k += L::NT)
+                if (cbase[v] + k < kCandCap) a.l1.cand[v][cbase[v] + k] = cbuf[v * L::CB + k];
+        }
+        float2* pbuf = reinterpret_cast<float2*>(red_d);
         const unsigned long long ns = block_sum(S.acc_s.n, red_u);
-        const double ss = block_sum(S.acc_s.s.value(), red_d);
+        const double ss = block_sum_pair(S.acc_s.s, pbuf);
         const unsigned long long nt = block_sum(S.acc_t.n, red_u);
-        const double st = block_sum(S.acc_t.s.value(), red_d);
+        const double st = block_sum_pair(S.acc_t.s, pbuf);
         if (tid == 0) {
             a.l1.k1_n[2 * cta] = ns;
             a.l1.k1_n[2 * cta + 1] = nt;
@@ -521,7 +591,7 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     for (int v = 0; v < 2; ++v) {
         L1Ctl& C = a.sc->ctl[v];
         const double r = a.sc->radius[v];
-        const bool win = v == 0 ? win_s : win_t;
+        const bool win = v == 0 ? W.s : W.t;
         if (!(r > 0.0)) {
             if (tid == 0) {
                 C.tau = __int_as_float(0x7f800000);
@@ -570,27 +640,10 @@ int tma_chunk(const Geom& g, int tiles) {
     return (g.n3 + chunks - 1) / chunks;
 }
 
-template <typename T>
-int launch_k1_tma_t(const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p, Scal* sc,
-                    const L1Work& w, cudaStream_t st) {
-    using L = Lay<T>;
-    K1TArgs<T> a;
-    a.g = g;
-    a.u_n = (T*)b.u_n; a.w1_n = (T*)b.w1_n; a.w2_n = (T*)b.w2_n; a.y1_n = (T*)b.y1_n; a.y2_n = (T*)b.y2_n;
-    a.p = p;
-    a.sc = sc;
-    a.l1 = w;
-    const int tx = (g.n2 + L::TX - 1) / L::TX, ty = (g.n1 + L::TY - 1) / L::TY;
-    a.chunk = tma_chunk(g, tx * ty);
-    dim3 grid(tx, ty, (g.n3 + a.chunk - 1) / a.chunk);
-    k1_tma<T><<<grid, L::NT, L::SMEM, st>>>(m, a);
-    return cudaGetLastError() == cudaSuccess ? 0 : -3;
-}
-
 }  // namespace
 
 int k1_tma_ctas(const Geom& g) {
-    const int tx = (g.n2 + 31) / 32, ty = (g.n1 + 15) / 16;
+    const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
     const int chunk = tma_chunk(g, tx * ty);
     return tx * ty * ((g.n3 + chunk - 1) / chunk);
 }
@@ -599,32 +652,42 @@ int k1_tma_ctas(const Geom& g) {
 // the cooperative-load kernel of k_stencil.cu).
 int k1_tma_configure(int storage) {
     if (storage != 0) return -1;
-    const cudaError_t e =
-        cudaFuncSetAttribute(k1_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay<float>::SMEM);
+    const cudaError_t e = cudaFuncSetAttribute(k1_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM);
     return e == cudaSuccess ? 0 : -3;
 }
 
 // tensor maps over the current-parity buffers of one iteration
 int k1_tma_maps(int storage, const Geom& g, const IterBufs& b, K1Maps* m) {
     if (storage != 0) return -1;
-    const int es = 4;
-    const int ox = 16 / es, sw = 32 + 2 * ox;
+    constexpr int sw = Lay::SW, ty = Lay::TY;
     int rc = 0;
-    rc |= tma_encode_cubes(&m->y1, b.y1, es, g.n1, g.n2, g.n3, g.p2, 2, sw, 16 + 4);
-    rc |= tma_encode_cubes(&m->y2, b.y2, es, g.n1, g.n2, g.n3, g.p2, 2, sw, 16 + 4);
-    rc |= tma_encode_cubes(&m->w1, b.w1, es, g.n1, g.n2, g.n3, g.p2, 6, sw, 16 + 2);
-    rc |= tma_encode_cubes(&m->w2, b.w2, es, g.n1, g.n2, g.n3, g.p2, 6, sw, 16 + 2);
-    rc |= tma_encode_cubes(&m->u, b.u, es, g.n1, g.n2, g.n3, g.p2, 1, sw, 16 + 1);
-    rc |= tma_encode_cubes(&m->q, b.q, es, g.n1, g.n2, g.n3, g.p2, 1, sw, 16 + 1);
-    rc |= tma_encode_cubes(&m->s, b.s, es, g.n1, g.n2, g.n3, g.p2, 1, 32, 16);
-    rc |= tma_encode_cubes(&m->t, b.t, es, g.n1, g.n2, g.n3, g.p2, 1, 32, 16);
-    rc |= tma_encode_cubes(&m->y3, b.y3, es, g.n1, g.n2, g.n3, g.p2, 1, 32, 16 + 1);
+    rc |= tma_encode_cubes(&m->y1, b.y1, 4, g.n1, g.n2, g.n3, g.p2, 2, sw, ty + 4);
+    rc |= tma_encode_cubes(&m->y2, b.y2, 4, g.n1, g.n2, g.n3, g.p2, 2, sw, ty + 4);
+    rc |= tma_encode_cubes(&m->w1, b.w1, 4, g.n1, g.n2, g.n3, g.p2, 6, sw, ty + 2);
+    rc |= tma_encode_cubes(&m->w2, b.w2, 4, g.n1, g.n2, g.n3, g.p2, 6, sw, ty + 2);
+    rc |= tma_encode_cubes(&m->u, b.u, 4, g.n1, g.n2, g.n3, g.p2, 1, sw, ty + 1);
+    rc |= tma_encode_cubes(&m->q, b.q, 4, g.n1, g.n2, g.n3, g.p2, 1, sw, ty + 1);
+    rc |= tma_encode_cubes(&m->s, b.s, 4, g.n1, g.n2, g.n3, g.p2, 1, Lay::TX, ty);
+    rc |= tma_encode_cubes(&m->t, b.t, 4, g.n1, g.n2, g.n3, g.p2, 1, Lay::TX, ty);
+    rc |= tma_encode_cubes(&m->y3, b.y3, 4, g.n1, g.n2, g.n3, g.p2, 1, Lay::TX, ty + 1);
     return rc ? -3 : 0;
 }
 
 int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p,
                   Scal* sc, const L1Work& w, cudaStream_t st) {
-    return storage == 0 ? launch_k1_tma_t<float>(g, m, b, p, sc, w, st) : -1;
+    if (storage != 0) return -1;
+    K1TArgs a;
+    a.g = g;
+    a.u_n = (float*)b.u_n; a.w1_n = (float*)b.w1_n; a.w2_n = (float*)b.w2_n;
+    a.y1_n = (float*)b.y1_n; a.y2_n = (float*)b.y2_n;
+    a.p = p;
+    a.sc = sc;
+    a.l1 = w;
+    const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
+    a.chunk = tma_chunk(g, tx * ty);
+    dim3 grid(tx, ty, (g.n3 + a.chunk - 1) / a.chunk);
+    k1_tma<<<grid, Lay::NT, Lay::SMEM, st>>>(m, a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 }  // namespace gsstv
