@@ -56,11 +56,14 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
     double tau = (s_hi + sum_c - r) / n_all;
     unsigned long long prev = m;
     for (int it = 0; it < 200; ++it) {
+        // for a float x, x > tau exactly when x > (tau rounded down to float):
+        // the test runs in FP32 (GB300's FP64 rate is a small fraction of it)
+        const float tf = __double2float_rd(tau);
         Kahan ka;
         unsigned long long c = 0;
         for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
             const float x = __ldcg(cand + k);
-            if ((double)x > tau) { ka.add(x); ++c; }
+            if (x > tf) { ka.add(x); ++c; }
         }
         const double sa = block_sum(ka.value(), red_d);
         const unsigned long long ca = block_sum(c, red_u);

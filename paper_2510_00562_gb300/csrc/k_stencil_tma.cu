@@ -20,6 +20,7 @@
 // the 12 w planes (1-pixel halo, w' written in place) fit beside u' of three
 // bands and D^T y2 of the previous band: about 216 KB of shared memory.
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "gsstv_internal.cuh"
@@ -634,10 +635,25 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     if (tid == 0) a.sc->k1_ticket = 0;
 }
 
+// Bands per CTA.  One CTA runs per SM, so a launch of U CTAs takes
+// ceil(U / 152) waves and the last wave leaves SMs idle; every CTA also pays a
+// prologue of about 1.5 band steps (its first copies, D^T y2 of the band
+// before, u' of its first band).  Picks the split of the bands (runs of at
+// least 8) that minimises idle fraction + prologue fraction.
 int tma_chunk(const Geom& g, int tiles) {
-    int chunks = (152 * 12 + tiles - 1) / tiles;            // about 12 CTAs per SM over the launch
-    chunks = std::max(1, std::min(chunks, (g.n3 + 7) / 8));
-    return (g.n3 + chunks - 1) / chunks;
+    constexpr double kSms = 152.0, kPrologue = 1.5;
+    const int max_chunks = std::max(1, g.n3 / 8);
+    int best_len = g.n3;
+    double best = 1e30;
+    for (int chunks = 1; chunks <= max_chunks; ++chunks) {
+        const int len = (g.n3 + chunks - 1) / chunks;
+        const int used = (g.n3 + len - 1) / len;               // chunks actually launched
+        const double units = (double)tiles * used;
+        const double waves = std::ceil(units / kSms);
+        const double waste = (waves - units / kSms) / waves + kPrologue / len;
+        if (waste < best - 1e-12) { best = waste; best_len = len; }
+    }
+    return best_len;
 }
 
 }  // namespace
