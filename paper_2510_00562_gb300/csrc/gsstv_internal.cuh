@@ -124,7 +124,8 @@ struct L1Ctl {
     int need;                  // L1Need
     double tau;                // threshold of the current iteration
     double tau_prev;           // threshold of the previous iteration
-    int have_tau, have_prev;
+    double tau_prev2;          // and of the one before
+    int have_tau, have_prev, have_prev2;
     double dens;               // candidates per unit of |x| at the last window
     // radix search
     unsigned prefix;           // key bits fixed by the previous levels
@@ -155,7 +156,8 @@ struct Scal {
 
 constexpr int kHistBins = 2048;        // radix histogram bins per vector
 constexpr unsigned kCandCap = 1u << 20; // candidate capacity per vector
-constexpr double kCandTarget = 65536.0; // window sized for about this many candidates
+constexpr double kCandTarget = 65536.0;  // K1's window is sized for at most about this many candidates
+constexpr double kRetryTarget = 262144.0; // a retry window after a miss: at most about this many
 constexpr unsigned kGatherMax = 1u << 16; // a radix bracket this small is gathered, a larger one refined
 
 // Device workspace of the l1 machinery (shared layout with the standalone

@@ -81,23 +81,30 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
 // with slope -#{|x| > tau}, so
 //   root above (phi(hi) > 0):  tau >= hi + phi(hi) / n_hi          (lower bound)
 //   root below (phi(lo) < 0):  tau <= lo + phi(lo) / n(lo)         (upper bound)
-// The retry window extends from the bound away from the old window by twice
-// the distance, capped near kCandTarget expected candidates.  Thread 0 only.
+// The retry window extends from the bound away from the old window by four
+// times the distance, capped near kRetryTarget expected candidates (wider than
+// K1's windows: one retry pass costs far less than the radix passes a second
+// miss leads to).  Thread 0 only.
 static __device__ void l1_after_miss(L1Ctl& c, int rc, const WinInfo& wi, double n_hi, unsigned m,
                                      double lo, double hi) {
+    // A retry needs a density estimate, and its capped width must cover at
+    // least half the jump the bound implies; otherwise it would most likely
+    // miss again and the radix passes run at once.
     double a = -1.0, b = -1.0;
-    if (rc == 2 && n_hi > 0.0) {
+    if (rc == 2 && n_hi > 0.0 && c.dens > 0.0) {
         const double lb = hi + wi.phi_hi / n_hi;
-        double w = fmax(2.0 * (lb - hi), 1e-6 * lb);
-        if (c.dens > 0.0) w = fmin(w, kCandTarget / c.dens);
-        a = lb;
-        b = lb + w;
-    } else if (rc == 1 && m <= kCandCap && wi.n_lo > 0.0 && lo > 0.0) {
+        const double w = fmin(fmax(4.0 * (lb - hi), 1e-6 * lb), kRetryTarget / c.dens);
+        if (w >= 0.5 * (lb - hi)) {
+            a = lb;
+            b = lb + w;
+        }
+    } else if (rc == 1 && m <= kCandCap && wi.n_lo > 0.0 && lo > 0.0 && c.dens > 0.0) {
         const double ub = lo + wi.phi_lo / wi.n_lo;
-        double w = fmax(2.0 * (lo - ub), 1e-6 * lo);
-        if (c.dens > 0.0) w = fmin(w, kCandTarget / c.dens);
-        a = fmax(ub - w, 0.0);
-        b = ub;
+        const double w = fmin(fmax(4.0 * (lo - ub), 1e-6 * lo), kRetryTarget / c.dens);
+        if (w >= 0.5 * (lo - ub)) {
+            a = fmax(ub - w, 0.0);
+            b = ub;
+        }
     }
     c.prefix = 0; c.n_above = 0; c.s_above = 0.0; c.exact_runs++;
     if (b > a && a >= 0.0) {
@@ -110,10 +117,15 @@ static __device__ void l1_after_miss(L1Ctl& c, int rc, const WinInfo& wi, double
 }
 
 // Records tau of this iteration and places the window of the next one around
-// the linear extrapolation of the last two thresholds.  The half-width covers
-// twice the last change and is capped so that about kCandTarget candidates
-// are expected (density measured at the last window).  Thread 0 only.
-static __device__ void l1_record_tau(L1Ctl& c, double tau_new, double m_used, double width_used) {
+// the linear extrapolation of the last two thresholds.  After a window hit the
+// half-width covers twice the last change of the step plus a tenth of the step
+// (the extrapolation error of a smoothly converging sequence); after a miss,
+// twice the step itself.  Either is capped so that about kCandTarget
+// candidates are expected (density measured at the last window).  `hit`: tau
+// came from K1's window.  Thread 0 only.
+static __device__ void l1_record_tau(L1Ctl& c, double tau_new, double m_used, double width_used, bool hit) {
+    c.tau_prev2 = c.tau_prev;
+    c.have_prev2 = c.have_prev;
     c.tau_prev = c.tau;
     c.have_prev = c.have_tau;
     c.tau = tau_new;
@@ -126,9 +138,18 @@ static __device__ void l1_record_tau(L1Ctl& c, double tau_new, double m_used, do
         c.window_ok = 1;
         return;
     }
-    const double d = c.have_prev ? fabs(tau_new - c.tau_prev) : 1e-3 * tau_new;
-    const double center = (c.have_prev && c.tau_prev > 0.0) ? tau_new + (tau_new - c.tau_prev) : tau_new;
-    double hw = 2.0 * d + 1e-7 * tau_new;
+    const bool trend = c.have_prev && c.tau_prev > 0.0;
+    const double d1 = trend ? tau_new - c.tau_prev : 0.0;
+    const double center = tau_new + d1;
+    double hw;
+    if (!trend) {
+        hw = 1e-3 * tau_new;
+    } else if (hit && c.have_prev2 && c.tau_prev2 > 0.0) {
+        const double d0 = c.tau_prev - c.tau_prev2;
+        hw = 2.0 * fabs(d1 - d0) + 0.1 * fabs(d1) + 1e-7 * tau_new;
+    } else {
+        hw = 2.0 * fabs(d1) + 1e-7 * tau_new;
+    }
     if (c.dens > 0.0) hw = fmin(hw, 0.5 * kCandTarget / c.dens);
     const double lo = fmax(center - hw, 0.0);
     const double hi = center + hw;
@@ -233,10 +254,10 @@ static __device__ void l1_radix_select(L1Ctl& c, RadixLevel lv, const unsigned l
         const unsigned key = lv.lo_key(c.prefix, kb);
         const double lo = key_value(key);
         if (best_phi == 0.0) {
-            l1_record_tau(c, lo, 0.0, 0.0);
+            l1_record_tau(c, lo, 0.0, 0.0, false);
         } else if (lv.level == 2) {
             // the bracket bin holds one value, inactive for any tau above it
-            l1_record_tau(c, (best_s_above - r) / (double)best_n_above, 0.0, 0.0);
+            l1_record_tau(c, (best_s_above - r) / (double)best_n_above, 0.0, 0.0, false);
         } else if (best_cnt <= (unsigned long long)kGatherMax) {
             c.need = NEED_GATHER;
             c.g_lo = __uint_as_float(key);
@@ -254,7 +275,7 @@ static __device__ void l1_radix_select(L1Ctl& c, RadixLevel lv, const unsigned l
         // phi(lower edge of the whole range) < 0: at level 0 the vector is
         // inside the ball; deeper, only rounding can get here.
         const double lo0 = lv.level == 0 ? 0.0 : key_value(lv.lo_key(c.prefix, 0));
-        l1_record_tau(c, lo0, 0.0, 0.0);
+        l1_record_tau(c, lo0, 0.0, 0.0, false);
     }
     __syncthreads();
 }

@@ -279,7 +279,7 @@ struct SearchArgs {
 // CTA selects the bracket.
 template <typename Src>
 __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a, const int level) {
-    extern __shared__ __align__(16) unsigned long long hsm[];   // [2][2048] counts, [2][2048] residues
+    extern __shared__ __align__(16) unsigned hsm[];   // [2][2048] counts, low and high residue halves
     __shared__ double sh_d[NT];
     __shared__ unsigned long long sh_u[NT];
     __shared__ int sh_i[1];
@@ -291,21 +291,24 @@ __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a,
     if (!need[0] && !need[1]) return;
     const RadixLevel lv{level};
     const int nb = lv.nbins();
-    unsigned long long* hc = hsm;
-    unsigned long long* hr = hsm + 2 * kHistBins;
-    for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) { hc[k] = 0; hr[k] = 0; }
+    // 32-bit shared bins: count, and the residue split into its low and high
+    // 10 bits so that a CTA's sums stay below 2^32 (it sees at most 2^21
+    // values per vector, each half below 2^10); every add is fire-and-forget,
+    // so no lane waits on a result
+    unsigned* hc = hsm;
+    unsigned* hrl = hsm + 2 * kHistBins;
+    unsigned* hrh = hsm + 4 * kHistBins;
+    for (int k = threadIdx.x; k < 6 * kHistBins; k += NT) hsm[k] = 0;
     __syncthreads();
     const unsigned pre0 = a.sc->ctl[0].prefix, pre1 = a.sc->ctl[1].prefix;
-    const int lane = threadIdx.x & 31;
-    // lanes that fall in the same bin add their count and residues once
     auto insert = [&](int v, bool take, unsigned key) {
-        const unsigned bn = take ? (unsigned)lv.bin(key) : 0xffffffffu;
-        const unsigned grp = __match_any_sync(0xffffffffu, bn);
         if (take) {
-            const unsigned tot = __reduce_add_sync(grp, lv.residue(key));
-            if (lane == __ffs(grp) - 1) {
-                atomicAdd(hc + v * kHistBins + bn, (unsigned long long)__popc(grp));
-                if (tot) atomicAdd(hr + v * kHistBins + bn, (unsigned long long)tot);
+            const int bn = v * kHistBins + lv.bin(key);
+            const unsigned r = lv.residue(key);
+            atomicAdd(hc + bn, 1u);
+            if (r) {
+                atomicAdd(hrl + bn, r & 1023u);
+                atomicAdd(hrh + bn, r >> 10);
             }
         }
     };
@@ -322,8 +325,9 @@ __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a,
     __syncthreads();
     for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) {
         if ((k % kHistBins) >= nb) continue;
-        if (hc[k]) atomicAdd(a.w.hcnt + k, hc[k]);
-        if (hr[k]) atomicAdd(a.w.hres + k, hr[k]);
+        if (hc[k]) atomicAdd(a.w.hcnt + k, (unsigned long long)hc[k]);
+        const unsigned long long res = ((unsigned long long)hrh[k] << 10) + hrl[k];
+        if (res) atomicAdd(a.w.hres + k, res);
     }
     __threadfence();
     __syncthreads();
@@ -340,6 +344,52 @@ __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a,
     if (threadIdx.x == 0) a.sc->fb_ticket = 0;
 }
 
+// Candidates of one CTA collected in shared memory and appended to the global
+// lists with one atomic per vector at the end of the pass (a warp-level global
+// atomic per candidate serialises on the counter once windows are wide).
+// What overflows the shared buffer goes straight to the global list.
+constexpr int kBlkCand = 1024;
+struct BlockCand {
+    float (*buf)[kBlkCand];
+    unsigned* cnt;     // [2]
+    unsigned* base;    // [2]
+    __device__ void init() {
+        if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+        __syncthreads();
+    }
+    __device__ void append(int v, bool take, float x, float* gcand, unsigned* gcnt) {
+        const unsigned mask = __ballot_sync(0xffffffffu, take);
+        if (mask == 0) return;
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(mask) - 1;
+        unsigned b = 0;
+        if (lane == leader) b = atomicAdd(cnt + v, (unsigned)__popc(mask));
+        b = __shfl_sync(0xffffffffu, b, leader);
+        const unsigned k = b + __popc(mask & ((1u << lane) - 1u));
+        if (take && k < (unsigned)kBlkCand) buf[v][k] = x;
+        if (b + __popc(mask) > (unsigned)kBlkCand) append_candidate(take && k >= (unsigned)kBlkCand, x, gcand, gcnt);
+    }
+    // whole block; before the pass's completion ticket
+    __device__ void flush(float* const* gcand, Scal* sc) {
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const unsigned n = min(cnt[threadIdx.x], (unsigned)kBlkCand);
+            base[threadIdx.x] = n ? atomicAdd(&sc->acc[threadIdx.x].m, n) : 0u;
+        }
+        __syncthreads();
+        for (int v = 0; v < 2; ++v) {
+            const unsigned n = min(cnt[v], (unsigned)kBlkCand);
+            for (unsigned k = threadIdx.x; k < n; k += blockDim.x)
+                if (base[v] + k < kCandCap) gcand[v][base[v] + k] = buf[v][k];
+        }
+    }
+};
+#define GSSTV_BLOCK_CAND(name)                                   \
+    __shared__ float name##_buf[2][kBlkCand];                    \
+    __shared__ unsigned name##_cnt[2], name##_base[2];           \
+    BlockCand name{name##_buf, name##_cnt, name##_base};         \
+    name.init()
+
 // Gathers the bracket bin of every vector that needs it and finishes tau.
 template <typename Src>
 __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a) {
@@ -352,10 +402,12 @@ __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a
     if (!need[0] && !need[1]) return;
     const float lo0 = a.sc->ctl[0].g_lo, hi0 = a.sc->ctl[0].g_hi;
     const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
+    GSSTV_BLOCK_CAND(bc);
     src.visit([&](bool valid, float x0, float x1) {
-        if (need[0]) append_candidate(valid && x0 > lo0 && x0 <= hi0, x0, a.w.cand[0], &a.sc->acc[0].m);
-        if (need[1]) append_candidate(valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
+        if (need[0]) bc.append(0, valid && x0 > lo0 && x0 <= hi0, x0, a.w.cand[0], &a.sc->acc[0].m);
+        if (need[1]) bc.append(1, valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
     });
+    bc.flush(a.w.cand, a.sc);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->g_ticket, 1u) == gridDim.x - 1);
@@ -379,7 +431,7 @@ __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a
             } else if (rc != 0) {
                 a.sc->error |= 2;
             }
-            l1_record_tau(C, tau, (double)min(m, kCandCap), ghi - glo);
+            l1_record_tau(C, tau, (double)min(m, kCandCap), ghi - glo, false);
             a.sc->acc[v].m = 0;
         }
         __syncthreads();
@@ -404,18 +456,20 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
     const float lo0 = a.sc->ctl[0].g_lo, hi0 = a.sc->ctl[0].g_hi;
     const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
     WinAcc w0, w1;
+    GSSTV_BLOCK_CAND(bc);
     src.visit([&](bool valid, float x0, float x1) {
         if (need[0]) {
             const bool hi = valid && x0 > hi0;
             if (hi) { w0.n++; w0.s.add(x0); }
-            append_candidate(valid && !hi && x0 > lo0, x0, a.w.cand[0], &a.sc->acc[0].m);
+            bc.append(0, valid && !hi && x0 > lo0, x0, a.w.cand[0], &a.sc->acc[0].m);
         }
         if (need[1]) {
             const bool hi = valid && x1 > hi1;
             if (hi) { w1.n++; w1.s.add(x1); }
-            append_candidate(valid && !hi && x1 > lo1, x1, a.w.cand[1], &a.sc->acc[1].m);
+            bc.append(1, valid && !hi && x1 > lo1, x1, a.w.cand[1], &a.sc->acc[1].m);
         }
     });
+    bc.flush(a.w.cand, a.sc);
     const unsigned long long n0 = block_sum(w0.n, red_u), n1 = block_sum(w1.n, red_u);
     const double s0 = block_sum(w0.s.value(), red_d), s1 = block_sum(w1.s.value(), red_d);
     if (threadIdx.x == 0) {
@@ -445,7 +499,7 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
         const int rc = l1_window_finish((double)n, sm, a.w.cand[v], m, lo, hi, a.sc->radius[v], &tau, red_d, red_u);
         if (threadIdx.x == 0) {
             if (rc == 0) {
-                l1_record_tau(C, tau, (double)min(m, kCandCap), hi - lo);
+                l1_record_tau(C, tau, (double)min(m, kCandCap), hi - lo, false);
             } else {
                 C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0;
             }
@@ -507,8 +561,11 @@ int launch_k2_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
 
 template <typename Src>
 int launch_radix_src(const Src& src, long long n, const SearchArgs& a, int level, cudaStream_t st) {
-    const size_t smem = 4 * kHistBins * sizeof(unsigned long long);
-    k_radix<Src><<<std::min(grid_for(n), 152 * 3), NT, smem, st>>>(src, a, level);
+    const size_t smem = 6 * kHistBins * sizeof(unsigned);
+    // enough CTAs that none sees more than 2^21 values (the shared bins are 32-bit)
+    const long long min_ctas = (n + (1ll << 21) - 1) >> 21;
+    const int grid = (int)std::max<long long>(std::min(grid_for(n), 152 * 3), min_ctas);
+    k_radix<Src><<<grid, NT, smem, st>>>(src, a, level);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -564,7 +621,7 @@ int launch_convert(const S* src, long long sp, long long sc_, D* dst, long long 
 }  // namespace
 
 int light_configure(int storage) {
-    const int smem = 4 * kHistBins * sizeof(unsigned long long);
+    const int smem = 6 * kHistBins * sizeof(unsigned);
     cudaError_t e = cudaErrorInvalidValue;
     switch (storage) {
         case 0: e = cudaFuncSetAttribute(k_radix<CubeSrc<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;

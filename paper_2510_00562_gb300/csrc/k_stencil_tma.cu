@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
         const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi);
         if (tid == 0) {
             if (!miss) {
-                l1_record_tau(C, tau, (double)min(m, kCandCap), thi - tlo);
+                l1_record_tau(C, tau, (double)min(m, kCandCap), thi - tlo, true);
                 C.hits++;
             } else {
                 l1_after_miss(C, miss, wi, (double)n, m, tlo, thi);
