@@ -195,6 +195,15 @@ template <typename X> __device__ __forceinline__ constexpr int set_of(X x) {
     else return X::value;
 }
 
+// Packed FP32 pairs (two lanes per instruction on sm_100 and later), used for
+// the (vertical, horizontal) pairs of the stencil; each lane rounds exactly as
+// the scalar operation would.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
+
 using Set0 = std::integral_constant<int, 0>;
 using Set1 = std::integral_constant<int, 1>;
 using Store = std::true_type;
@@ -220,11 +229,11 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     const int blast = min(b1, g.n3 - 1);
 
     // ---- ring slots ----
-    auto ygb = [&](int band) { return sm + ((band - bstart) % L::NYS) * L::YG_B; };
-    auto wgb = [&](int band) { return sm + L::OFF_WG + ((band - b0) % L::NWS) * L::WG_B; };
+    auto ygb = [&](int band) { return sm + ((unsigned)(band - bstart) % L::NYS) * L::YG_B; };
+    auto wgb = [&](int band) { return sm + L::OFF_WG + ((unsigned)(band - b0) % L::NWS) * L::WG_B; };
     auto yg = [&](int band) { return reinterpret_cast<const float*>(ygb(band)); };
     auto wg = [&](int band) { return reinterpret_cast<float*>(wgb(band)); };
-    auto upl = [&](int band) { return up + (band % L::NUS) * L::UP1; };
+    auto upl = [&](int band) { return up + ((unsigned)band % L::NUS) * L::UP1; };
 
     auto issue_y = [&](int band) {
         unsigned char* s = ygb(band);
@@ -250,9 +259,9 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
         S.n_w++;
     };
     auto wait_y = [&](int band) {
-        return mbar_wait(ybar + (band - bstart) % L::NYS, ((band - bstart) / L::NYS) & 1);
+        return mbar_wait(ybar + (unsigned)(band - bstart) % L::NYS, ((unsigned)(band - bstart) / L::NYS) & 1);
     };
-    auto wait_w = [&](int band) { return mbar_wait(wbar + (band - b0) % L::NWS, ((band - b0) / L::NWS) & 1); };
+    auto wait_w = [&](int band) { return mbar_wait(wbar + (unsigned)(band - b0) % L::NWS, ((unsigned)(band - b0) / L::NWS) & 1); };
 
     // D^T y = D_v^T y_v + D_h^T y_h at tile-relative (r, c); yv, yh: y planes
     auto dty = [&](const float* yv, const float* yh, int r, int c) {
@@ -276,8 +285,17 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
         if constexpr (EDGE) {
             if (i0 + r >= g.n1 || j0 + c >= g.n2) { upb[kc] = 0.f; gs[kc] = 0.f; return; }
         }
-        const float d1 = dty(ys, ys + YPL, r, c);
-        const float gcur = dty(ys + 2 * YPL, ys + 3 * YPL, r, c);
+        float d1, gcur;                                 // D^T y1 and D^T y2 of the band
+        if constexpr (EDGE) {
+            d1 = dty(ys, ys + YPL, r, c);
+            gcur = dty(ys + 2 * YPL, ys + 3 * YPL, r, c);
+        } else {
+            const int k = (r + 2) * SW + (c + OX);
+            const float *v1 = ys + k, *h1 = ys + YPL + k, *v2 = ys + 2 * YPL + k, *h2 = ys + 3 * YPL + k;
+            const float2 d = sub2(add2(sub2(f2(v1[-SW], v2[-SW]), f2(v1[0], v2[0])), f2(h1[-1], h2[-1])), f2(h1[0], h2[0]));
+            d1 = d.x;
+            gcur = d.y;
+        }
         const float gprev = gs[kc];
         float dst_ = 0.f;
         if (bb >= 1) dst_ += gprev;
@@ -320,13 +338,16 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
         };
         const float v00 = V(0, 0), vm0 = V(-1, 0), v01 = V(0, 1), vm1 = V(-1, 1);
         const float h00 = H(0, 0), h0m = H(0, -1), h10 = H(1, 0), h1m = H(1, -1);
-        float Lv[3], Lh[3];
-        Lv[0] = mv ? v00 : 0.f;
-        Lh[0] = mv ? 0.25f * (h00 + h0m + h10 + h1m) : 0.f;
-        Lv[1] = mh ? 0.25f * (v00 + vm0 + v01 + vm1) : 0.f;
-        Lh[1] = mh ? h00 : 0.f;
-        Lv[2] = 0.5f * (v00 + vm0);
-        Lh[2] = 0.5f * (h00 + h0m);
+        // (v, h) pairs: the centred means 0.5 (v00 + vm0), 0.5 (h00 + h0m), and
+        // the four-point means 0.25 (v00 + vm0 + v01 + vm1), 0.25 (h00 + h0m + h10 + h1m)
+        float2 sum = add2(f2(v00, h00), f2(vm0, h0m));
+        const float2 cen = mul2(sum, f2(0.5f, 0.5f));
+        sum = add2(add2(sum, f2(v01, h10)), f2(vm1, h1m));
+        const float2 four = mul2(sum, f2(0.25f, 0.25f));
+        float2 Lg[3];                                   // (L_v, L_h) of the three grids
+        Lg[0] = f2(mv ? v00 : 0.f, mv ? four.y : 0.f);
+        Lg[1] = f2(mh ? four.x : 0.f, mh ? h00 : 0.f);
+        Lg[2] = cen;
         const float gam = set ? P.gamma_w2 : P.gamma_w1;
         const float thr = set ? P.thr_w2 : P.thr_w1;
         const float thr2 = thr * thr;
@@ -335,11 +356,13 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
         for (int gr = 0; gr < 3; ++gr) {
             const float wv = wp[(2 * gr) * WPL];
             const float wh = wp[(2 * gr + 1) * WPL];
-            const float xv = wv + gam * Lv[gr], xh = wh + gam * Lh[gr];
+            const float2 x = fma2(f2(gam, gam), Lg[gr], f2(wv, wh));
+            const float xv = x.x, xh = x.y;
             // Eq. 24: max(1 - thr / ||x||, 0) x, with 1 / ||x|| from rsqrt
             const float n2 = xv * xv + xh * xh;
             const float sc = n2 > thr2 ? fmaxf(1.f - thr * rsqrtf(n2), 0.f) : 0.f;
-            const float nv = sc * xv, nh = sc * xh;
+            const float2 nn = mul2(f2(sc, sc), x);
+            const float nv = nn.x, nh = nn.y;
             wp[(2 * gr) * WPL] = 2.f * nv - wv;
             wp[(2 * gr + 1) * WPL] = 2.f * nh - wh;
             if constexpr (decltype(store_c)::value) {
@@ -388,13 +411,15 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
         const int kc = r_t * UC + c_t;
         const float u0 = upb[kc];
         const bool mv = !EDGE || gi_t < g.n1 - 1, mh = !EDGE || gj_t < g.n2 - 1;
-        const float duv = mv ? upb[kc + UC] - u0 : 0.f;
-        const float duh = mh ? upb[kc + 1] - u0 : 0.f;
+        // (vertical, horizontal) pairs: D u' and D D_s u' at the voxel
+        const float2 ub = f2(upb[kc + UC], upb[kc + 1]);
+        const float2 du_ = sub2(ub, f2(u0, u0));
+        const float2 du = f2(mv ? du_.x : 0.f, mh ? du_.y : 0.f);
         const float d0 = upn[kc] - u0;
-        const float ddv = nxt && mv ? (upn[kc + UC] - upb[kc + UC]) - d0 : 0.f;
-        const float ddh = nxt && mh ? (upn[kc + 1] - upb[kc + 1]) - d0 : 0.f;
+        const float2 dd_ = sub2(sub2(f2(upn[kc + UC], upn[kc + 1]), ub), f2(d0, d0));
+        const float2 dd = f2(nxt && mv ? dd_.x : 0.f, nxt && mh ? dd_.y : 0.f);
         const float* wk = wp + (r_t + 1) * SW + (c_t + OX);
-        float gv[2], gh[2];
+        float2 lt[2];                                    // (L^T w')_v, (L^T w')_h of each set
 #pragma unroll
         for (int set = 0; set < 2; ++set) {
             auto Wk = [&](int k, int dr, int dc) { return wk[(6 * set + k) * WPL + dr * SW + dc]; };
@@ -406,18 +431,21 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
                 if constexpr (EDGE) return (gj_t + dc < g.n2 - 1) ? Wk(2, dr, dc) : 0.f;
                 else return Wk(2, dr, dc);
             };
-            gv[set] = mv ? (Wk(0, 0, 0) + 0.25f * (B_(0, 0) + B_(1, 0) + B_(0, -1) + B_(1, -1))
-                            + 0.5f * (Wk(4, 0, 0) + Wk(4, 1, 0)))
-                         : 0.f;
-            gh[set] = mh ? (0.25f * (A_(0, 0) + A_(0, 1) + A_(-1, 0) + A_(-1, 1)) + Wk(3, 0, 0)
-                            + 0.5f * (Wk(5, 0, 0) + Wk(5, 0, 1)))
-                         : 0.f;
+            // v: W0 + 0.25 (B(0,0) + B(1,0) + B(0,-1) + B(1,-1)) + 0.5 (W4(0,0) + W4(1,0))
+            // h: W3 + 0.25 (A(0,0) + A(0,1) + A(-1,0) + A(-1,1)) + 0.5 (W5(0,0) + W5(0,1))
+            const float2 s4 = add2(add2(add2(f2(B_(0, 0), A_(0, 0)), f2(B_(1, 0), A_(0, 1))), f2(B_(0, -1), A_(-1, 0))),
+                                   f2(B_(1, -1), A_(-1, 1)));
+            const float2 s2 = add2(f2(Wk(4, 0, 0), Wk(5, 0, 0)), f2(Wk(4, 1, 0), Wk(5, 0, 1)));
+            const float2 gg = fma2(f2(0.5f, 0.5f), s2, fma2(f2(0.25f, 0.25f), s4, f2(Wk(0, 0, 0), Wk(3, 0, 0))));
+            lt[set] = f2(mv ? gg.x : 0.f, mh ? gg.y : 0.f);
         }
         const unsigned ob = (unsigned)tb * plane + o_t;
-        a.y1_n[ob] = yc[0] + P.gamma_y1 * (duv - gv[0]);
-        a.y1_n[cube + ob] = yc[1] + P.gamma_y1 * (duh - gh[0]);
-        a.y2_n[ob] = yc[2] + P.gamma_y2 * (ddv - gv[1]);
-        a.y2_n[cube + ob] = yc[3] + P.gamma_y2 * (ddh - gh[1]);
+        const float2 y1 = fma2(f2(P.gamma_y1, P.gamma_y1), sub2(du, lt[0]), f2(yc[0], yc[1]));
+        const float2 y2 = fma2(f2(P.gamma_y2, P.gamma_y2), sub2(dd, lt[1]), f2(yc[2], yc[3]));
+        a.y1_n[ob] = y1.x;
+        a.y1_n[cube + ob] = y1.y;
+        a.y2_n[ob] = y2.x;
+        a.y2_n[cube + ob] = y2.y;
     };
 
     // ---- l1 window statistics of s~, t~ at this thread's voxel ----
@@ -463,11 +491,12 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     __syncthreads();
 
     // ---- band march, one barrier per band ----
-    // The tile work of a band is one straight run (w steps, the ascent of the
-    // previous band, u' of the next, the statistics) so that the compiler can
-    // interleave their independent chains; the ring work follows.  u' of the
-    // band past the cube's last one is computed from a stale slot and not
-    // stored (its values are never used).
+    // The ascent of the previous band needs nothing from this band's copies,
+    // so it runs before the waits on them; then the tile work of the band
+    // (the statistics, w steps, u' of the next band) is one straight run so
+    // that the compiler can interleave its independent chains, and the ring
+    // work follows.  u' of the band past the cube's last one is computed from
+    // a stale slot and not stored (its values are never used).
     float yprev[4] = {0.f, 0.f, 0.f, 0.f};
     auto step = [&](int b, auto do_t) -> bool {
         const bool has_next = b + 1 < g.n3;
@@ -475,6 +504,7 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
             if (b + 2 <= blast && b + 2 - bstart >= L::NYS) issue_y(b + 2);
             if (b + 2 < b1) issue_w(b + 2);
         }
+        if constexpr (decltype(do_t)::value) t_item(b - 1, yprev);
         bool okb = wait_w(b);
         if (has_next) okb = wait_y(b + 1) && okb;
         okb = __all_sync(0xffffffffu, okb);   // warp-uniform: the statistics use warp votes
@@ -487,11 +517,10 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
             float ycur[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) ycur[k] = ys[k * YPL + ky_t];
+            if (W.s || W.t) stats(ys);
             w_item(Set0{}, Store{}, ys, wst, r_t, c_t, a.w1_n + ob, valid_t);
             w_item(Set1{}, Store{}, ys, wst, r_t, c_t, a.w2_n + ob, valid_t);
-            if constexpr (decltype(do_t)::value) t_item(b - 1, yprev);
             u_item(Store{}, ysn, upn, b + 1, r_t, c_t, a.u_n + (ob + plane), valid_t && b + 1 < b1);
-            if (W.s || W.t) stats(ys);
             if (has_rw) w_item(rw_set, NoStore{}, ys, wst, rw_r, rw_c, nullptr, false);
             if (has_ru && has_next) u_item(NoStore{}, ysn, upn, b + 1, ru_r, ru_c, nullptr, false);
 #pragma unroll
