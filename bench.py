@@ -44,6 +44,7 @@ K1_WORDS = 38
 ITER_WORDS = 49
 FLOOR_WORDS_FP32 = 43                     # every state word read and written once, v read once
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0       # GB300 HBM3e nominal, reported beside the measured peak
 CPU_SAMPLE = (128, 128, 224)              # spatial crop of the workload for the oracle timing
 
 
@@ -250,7 +251,7 @@ def run_gpu(args):
     import numpy as np
     import torch
 
-    from paper_2510_00562_gb300 import build, synth
+    from paper_2510_00562_gb300 import build, metrics, synth
     from paper_2510_00562_gb300.solver import GeoSSTVSolver, make_params
 
     rank, world, local = _env_rank()
@@ -291,7 +292,7 @@ def run_gpu(args):
 
     pf = None
     if not args.no_precision_form and args.storage == "fp32" and world == 1:
-        pf = precision_form(sol, pb, args)
+        pf = precision_form(sol, pb, args.shape, args.pf_iters, args.steps)
 
     # end to end through the public host API: copies in, solve, copies out
     sol.set_params(make_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03,
@@ -308,6 +309,16 @@ def run_gpu(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     e2e_value = world * nvox * args.steps / e2e_s
     sol.close()
+    quality = None
+    if rank == 0:
+        # Sec. IV-A metrics of the end-to-end result (`steps` iterations from the
+        # initial point) against the clean cube; MSSIM on every 8th band to keep
+        # the host time short
+        u_np = uh.numpy()
+        quality = {"iterations": args.steps,
+                   "mpsnr_db": metrics.mpsnr(u_np, pb["u_bar"]),
+                   "mssim_every_8th_band": metrics.mssim(u_np[::8], pb["u_bar"][::8]),
+                   "observation_mpsnr_db": metrics.mpsnr(pb["v"], pb["u_bar"])}
 
     if rank != 0:
         return 0
@@ -331,6 +342,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": K1_KERNEL[variant],
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} copy bandwidth",
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                      "traffic": traffic_bpv * nvox if traffic_bpv else None,
                      "algorithmic_bytes": k1_bytes, "k1_ms": k1_ms},
         "iteration_bandwidth": {
@@ -343,6 +355,7 @@ def run_gpu(args):
                 "note": "one gsstv_solve_host call of `steps` iterations: pinned H2D of v, "
                         "state reset, iterations, D2H of u, s, t"},
         "gpu_launches": 7 * args.steps,
+        "quality": quality,
     }
     if pf:
         line["precision_form"] = pf
@@ -360,7 +373,7 @@ def run_gpu(args):
     return 0
 
 
-def precision_form(sol32, pb, args):
+def precision_form(sol32, pb, shape, N, steps_after):
     """Mixed storage vs FP32 on the same cube and iteration budget N: FP32 for N
     passes, against BF16 iterates (FP32 arithmetic) for 0.8 N passes followed
     by an FP32 phase of 0.2 N passes warm-started from the 16-bit state.
@@ -369,9 +382,8 @@ def precision_form(sol32, pb, args):
     import torch
     from paper_2510_00562_gb300 import metrics
     from paper_2510_00562_gb300.solver import GeoSSTVSolver, make_params
-    n1, n2, n3 = args.shape
+    n1, n2, n3 = shape
     nvox = n1 * n2 * n3
-    N = args.pf_iters
     n16 = (N * 4) // 5
     kw = dict(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03, graph_iters=16)
     v = torch.from_numpy(pb["v"]).cuda()
@@ -407,8 +419,27 @@ def precision_form(sol32, pb, args):
         out[storage] = {"passes_16bit": n16, "passes_fp32": N - n16,
                         "value_16bit_phase": nvox * n16 / (ms * 1e-3), "unit": UNIT,
                         "mpsnr_after_16bit_db": m16, "mpsnr_db": mf, "delta_vs_fp32_db": mf - m32}
-    sol32.set_params(make_params(max_iter=args.steps, **kw))
+    sol32.set_params(make_params(max_iter=steps_after, **kw))
     return out
+
+
+def run_precision_study(args):
+    """The precision form on a cube of its own (default 1024x1024x200, 5000
+    iterations: 4000 16-bit + 1000 FP32 against 5000 FP32), one JSON line."""
+    import torch
+    from paper_2510_00562_gb300 import synth
+    from paper_2510_00562_gb300.solver import GeoSSTVSolver, make_params
+    n1, n2, n3 = (int(x) for x in args.precision_study.split("x"))
+    pb = synth.make_problem(n1, n2, n3, seed=0, noise=synth.NoiseSpec(**NOISE))
+    stream = torch.cuda.current_stream()
+    with GeoSSTVSolver(n1, n2, n3, make_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"],
+                                               omega=0.03, graph_iters=16), stream=stream) as sol32:
+        t0 = time.perf_counter()
+        out = precision_form(sol32, pb, (n1, n2, n3), args.pf_iters, args.pf_iters)
+        wall = time.perf_counter() - t0
+    print(json.dumps({"precision_study": {"cube": f"{n1}x{n2}x{n3}", "data": "synthetic",
+                                          "noise": NOISE, "wall_s": wall, **out}}), flush=True)
+    return 0
 
 
 def main(argv=None):
@@ -423,6 +454,9 @@ def main(argv=None):
     ap.add_argument("--no-precision-form", action="store_true")
     ap.add_argument("--pf-iters", type=int, default=500,
                     help="iteration budget of the mixed-vs-FP32 comparison")
+    ap.add_argument("--precision-study", default=None, metavar="N1xN2xN3",
+                    help="run only the mixed-vs-FP32 comparison on a cube of this size "
+                         "(with --pf-iters 5000 for the 4000 + 1000 split) and print one JSON line")
     ap.add_argument("--shape", default="512x512x224",
                     help="N1xN2xN3; anything but the default is a profiling case, not a bench line")
     args = ap.parse_args(argv)
@@ -431,6 +465,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_study:
+        return run_precision_study(args)
     return run_gpu(args)
 
 
