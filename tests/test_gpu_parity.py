@@ -218,6 +218,28 @@ def test_per_band_constant_fixed_point_exact(shape):
             assert not st[k].any(), k
 
 
+def test_full_size_one_pass_512x512x224():
+    """One pass of Algorithm 1 on the benchmark's 512x512x224 cube from a
+    random state, with the kernels and run lengths the benchmark times, against
+    one FP64 oracle pass over the whole cube: every variable within the bound
+    of the small-cube one-pass test."""
+    n1, n2, n3 = 512, 512, 224
+    rs, v, kw = _random_problem(n1, n2, n3, seed=2024)
+    p = make_params(graph_iters=0, **kw)
+    with GeoSSTVSolver(n1, n2, n3, p) as sol:
+        sol.load(to_dev(v))
+        sol.set_state({k: to_dev(rs[k]) for k in KEYS})
+        sol.iterate(1)
+        got = sol.get_state()
+    ref = o.ppds_step(o.State(**{k: rs[k].astype(np.float64) for k in KEYS}), v.astype(np.float64),
+                      oracle_params(p))
+    del rs
+    for k in KEYS:
+        e = rel(got[k].cpu().numpy(), getattr(ref, k))
+        print(f"full-size one pass {k}: {e:.3e}")
+        assert e < 2e-6, (k, e)
+
+
 def test_full_size_invariants_512x512x224():
     """The benchmark cube in the benchmark's launch configuration: the
     projected constraints hold after every pass (l1 balls, box)."""
