@@ -122,9 +122,16 @@ struct K1Win {
     float lo_s, hi_s, lo_t, hi_t;
 };
 
+// A thread's window statistics: count (a CTA covers at most a few thousand
+// voxels per thread slot, so 32 bits suffice) and compensated sum.
+struct K1Acc {
+    unsigned n = 0;
+    Kahan s;
+};
+
 // Per-CTA running state shared by the two tile paths.
 struct K1State {
-    WinAcc acc_s, acc_t;
+    K1Acc acc_s, acc_t;
     unsigned n_y = 0, n_w = 0;   // groups issued so far (thread 0 only)
 };
 
@@ -181,10 +188,10 @@ __device__ double block_sum_pair(const Kahan& k, float2* buf) {
 }
 
 // Counts x into a window accumulator when `take`, without a branch.
-__device__ __forceinline__ void win_add(WinAcc& A, bool take, float x) {
+__device__ __forceinline__ void win_add(K1Acc& A, bool take, float x) {
     Kahan k = A.s;
     k.add(x);
-    A.n += take ? 1ull : 0ull;
+    A.n += take ? 1u : 0u;
     A.s.s = take ? k.s : A.s.s;
     A.s.c = take ? k.c : A.s.c;
 }
@@ -452,19 +459,29 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     auto stats = [&](const float* ys) {
         float xs = 0.f, xt = 0.f;
         if (valid_t) {
+            // s~ = s - g_s y4, t~ = t - g_t (D_v^T y3 + y4), each product and
+            // difference rounded once as in s_t_tilde (the light pass computes
+            // the same values), the (s, t) pair packed
             const float qv = ys[L::O_Q + r_t * SW + (c_t + OX)];
             const float y3v = ys[L::O_Y3 + (r_t + 1) * TX + c_t];
             const float y3u = (!EDGE || gi_t >= 1) ? ys[L::O_Y3 + r_t * TX + c_t] : 0.f;
-            s_t_tilde(ys[L::O_S + r_t * TX + c_t], ys[L::O_T + r_t * TX + c_t], y3v, y3u, qv, cs, gi_t, g.n1,
-                      P.gamma_s, P.gamma_t, xs, xt);
+            const float y4 = __fmul_rn(cs, qv);
+            const float dvt = __fsub_rn(y3u, gi_t <= g.n1 - 2 ? y3v : 0.f);
+            const float2 m = mul2(f2(P.gamma_s, P.gamma_t), f2(y4, __fadd_rn(dvt, y4)));
+            const float2 x = sub2(f2(ys[L::O_S + r_t * TX + c_t], ys[L::O_T + r_t * TX + c_t]), m);
+            xs = x.x;
+            xt = x.y;
         }
         // an inactive window has lo = hi = +inf: nothing is counted or taken
         const float x_s = fabsf(xs), x_t = fabsf(xt);
         const bool hs = valid_t && x_s > W.hi_s, ht = valid_t && x_t > W.hi_t;
         win_add(S.acc_s, hs, x_s);
         win_add(S.acc_t, ht, x_t);
-        append_shared(valid_t && !hs && x_s > W.lo_s, x_s, cbuf, ccnt, a.l1.cand[0], &a.sc->acc[0].m);
-        append_shared(valid_t && !ht && x_t > W.lo_t, x_t, cbuf + L::CB, ccnt + 1, a.l1.cand[1], &a.sc->acc[1].m);
+        const bool cs_ = valid_t && !hs && x_s > W.lo_s, ct_ = valid_t && !ht && x_t > W.lo_t;
+        if (__ballot_sync(0xffffffffu, cs_ || ct_)) {     // most warps have no candidate
+            append_shared(cs_, x_s, cbuf, ccnt, a.l1.cand[0], &a.sc->acc[0].m);
+            append_shared(ct_, x_t, cbuf + L::CB, ccnt + 1, a.l1.cand[1], &a.sc->acc[1].m);
+        }
     };
 
     // ---- prologue: D^T y2 of band b0-1 and u' of band b0 ----
@@ -601,9 +618,9 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
                 if (cbase[v] + k < kCandCap) a.l1.cand[v][cbase[v] + k] = cbuf[v * L::CB + k];
         }
         float2* pbuf = reinterpret_cast<float2*>(red_d);
-        const unsigned long long ns = block_sum(S.acc_s.n, red_u);
+        const unsigned long long ns = block_sum((unsigned long long)S.acc_s.n, red_u);
         const double ss = block_sum_pair(S.acc_s.s, pbuf);
-        const unsigned long long nt = block_sum(S.acc_t.n, red_u);
+        const unsigned long long nt = block_sum((unsigned long long)S.acc_t.n, red_u);
         const double st = block_sum_pair(S.acc_t.s, pbuf);
         if (tid == 0) {
             a.l1.k1_n[2 * cta] = ns;
