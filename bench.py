@@ -423,6 +423,86 @@ def precision_form(sol32, pb, shape, N, steps_after):
     return out
 
 
+BATCH_SIDES = (32, 48, 96, 128, 256, 512)
+BATCH_BANDS = (31, 64, 128, 224)
+
+
+def batch_workload(ncubes, seed=0):
+    """Uneven cubes: N1, N2 drawn independently from BATCH_SIDES, N3 from
+    BATCH_BANDS; Gaussian sigma ~ U[0.02, 0.15], salt-and-pepper and stripe
+    rates ~ U[0, 0.15]."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(ncubes):
+        n1, n2 = (int(x) for x in rng.choice(BATCH_SIDES, 2))
+        n3 = int(rng.choice(BATCH_BANDS))
+        out.append((n1, n2, n3, float(rng.uniform(0.02, 0.15)), float(rng.uniform(0.0, 0.15)),
+                    float(rng.uniform(0.0, 0.15))))
+    return out
+
+
+def run_batch(args):
+    """Many uneven cubes, each with its own Eq. 28 stopping rule (< 1e-5, at
+    most 3000 passes): the batch solver against looping the plain solver over
+    the same cubes.  One JSON line."""
+    # more hardware work queues than the default 8, so that the cubes' streams
+    # do not share queues (read when the CUDA context is created)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import numpy as np
+    import torch
+    from paper_2510_00562_gb300 import synth
+    from paper_2510_00562_gb300.solver import GeoSSTVBatch, GeoSSTVSolver, make_params
+    cubes = batch_workload(args.batch)
+    pbs, params, vs = [], [], []
+    for k, (n1, n2, n3, sg, ps, pt) in enumerate(cubes):
+        pb = synth.make_problem(n1, n2, n3, seed=1000 + k,
+                                noise=synth.NoiseSpec(sigma=sg, sp_rate=ps, stripe_rate=pt, stripe_amp=0.25))
+        params.append(make_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03,
+                                  tol=1e-5, check_every=50, max_iter=3000, graph_iters=16))
+        vs.append(torch.from_numpy(pb["v"]).cuda())
+        pbs.append(pb)
+    shapes = [c[:3] for c in cubes]
+    vox = np.array([n1 * n2 * n3 for n1, n2, n3 in shapes], dtype=np.float64)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    with GeoSSTVBatch(shapes, params) as bt:
+        bt.solve(vs)                                     # graphs built
+        (us, _, _, done_b), t_batch = timed(lambda: bt.solve(vs))
+    sols = [GeoSSTVSolver(n1, n2, n3, p) for (n1, n2, n3), p in zip(shapes, params)]
+
+    def loop():
+        res = [s.solve(v) for s, v in zip(sols, vs)]
+        return [r[0] for r in res], [r[3] for r in res]
+
+    loop()                                               # graphs built
+    (u_loop, done_l), t_loop = timed(loop)
+    dmax = max(float((a - b).abs().max().item()) for a, b in zip(us, u_loop))
+    for s_ in sols:
+        s_.close()
+    vi_b = float((vox * np.array(done_b)).sum())
+    vi_l = float((vox * np.array(done_l)).sum())
+    line = {"batch": {
+        "cubes": len(cubes), "data": "synthetic",
+        "workload": "N1, N2 from {32,48,96,128,256,512}, N3 from {31,64,128,224}, sigma ~ U[0.02,0.15], "
+                    "salt-and-pepper and stripe rates ~ U[0,0.15]; Eq. 28 < 1e-5 checked every 50 passes, "
+                    "at most 3000 passes",
+        "voxels": float(vox.sum()), "passes": {"min": int(min(done_b)), "median": float(np.median(done_b)),
+                                               "max": int(max(done_b))},
+        "batch_s": t_batch, "batch_value": vi_b / t_batch,
+        "loop_s": t_loop, "loop_value": vi_l / t_loop, "unit": UNIT,
+        "speedup": t_loop / t_batch, "same_passes": list(done_b) == list(done_l),
+        "max_abs_u_diff": dmax}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_precision_study(args):
     """The precision form on a cube of its own (default 1024x1024x200, 5000
     iterations: 4000 16-bit + 1000 FP32 against 5000 FP32), one JSON line."""
@@ -457,6 +537,8 @@ def main(argv=None):
     ap.add_argument("--precision-study", default=None, metavar="N1xN2xN3",
                     help="run only the mixed-vs-FP32 comparison on a cube of this size "
                          "(with --pf-iters 5000 for the 4000 + 1000 split) and print one JSON line")
+    ap.add_argument("--batch", type=int, default=0, metavar="NCUBES",
+                    help="run only the batch measurement on NCUBES uneven cubes and print one JSON line")
     ap.add_argument("--shape", default="512x512x224",
                     help="N1xN2xN3; anything but the default is a profiling case, not a bench line")
     args = ap.parse_args(argv)
@@ -467,6 +549,8 @@ def main(argv=None):
         return run_reference(args)
     if args.precision_study:
         return run_precision_study(args)
+    if args.batch:
+        return run_batch(args)
     return run_gpu(args)
 
 

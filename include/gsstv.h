@@ -159,6 +159,37 @@ int gsstv_set_timing(gsstv_handle* h, int on);
 /* Bytes the handle holds on the device. */
 int64_t gsstv_device_bytes(const gsstv_handle* h);
 
+/* ---- batches of independent cubes ------------------------------------------
+ * Algorithm 1 on many cubes of different shapes at once (each cube its own
+ * problem, with its own parameters and its own Eq. 28 stopping rule).  A
+ * batch holds one solver per cube, each on a stream of its own; a solve keeps
+ * a block of passes (check_every, or max_iter when tol = 0) in flight for
+ * every unfinished cube and applies each cube's stopping rule as gsstv_iterate
+ * does, so every cube gets exactly the result gsstv_solve gives it alone.
+ *
+ * gsstv_batch_create: ncubes >= 1; n1, n2, n3, params: ncubes entries each
+ * (host arrays, read during the call); each cube obeys gsstv_create's limits.
+ * stream: the caller's cudaStream_t (or NULL); solves start after the work
+ * already queued on it.  Errors: GSSTV_ERR_ARG, GSSTV_ERR_OOM, GSSTV_ERR_CUDA;
+ * nothing is left allocated on an error.
+ *
+ * gsstv_batch_solve: d_v, d_u (and d_s, d_t unless NULL): host arrays of
+ * ncubes device pointers, each to a C-contiguous (N3, N1, N2) float32 cube of
+ * that cube's shape, owned by the caller; iters_done (NULL or ncubes ints)
+ * receives the passes each cube ran.  Returns when every cube has finished;
+ * on an error no work of the batch is left in flight. */
+typedef struct gsstv_batch gsstv_batch;
+int gsstv_batch_create(gsstv_batch** b, int ncubes, const int* n1, const int* n2, const int* n3,
+                       const gsstv_params* params, void* stream);
+int gsstv_batch_solve(gsstv_batch* b, const float* const* d_v, float* const* d_u,
+                      float* const* d_s, float* const* d_t, int* iters_done);
+/* Number of cubes; the solver of cube c (owned by the batch: not destroyed
+ * by the caller), e.g. for gsstv_get_stats. */
+int gsstv_batch_size(const gsstv_batch* b);
+int gsstv_batch_handle(gsstv_batch* b, int c, gsstv_handle** out);
+/* Releases the batch and every solver in it.  NULL is accepted. */
+int gsstv_batch_destroy(gsstv_batch* b);
+
 /* Projection onto the l1 ball {z : ||z||_1 <= radius} (Sec. III-B, the prox
  * of the indicator of B_{1,alpha}): d_out = sign(x) max(|x| - tau, 0), with
  * tau >= 0 the root of sum max(|x_i| - tau, 0) = radius, or d_out = d_x when

@@ -77,6 +77,15 @@ _SIGS = {
                                      ctypes.POINTER(c_double), c_void_p]),
     "gsstv_project_l1ball_noalloc": (c_int, [c_void_p, c_int64, c_double, c_void_p,
                                              ctypes.POINTER(c_double), c_void_p]),
+    "gsstv_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int),
+                                   ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                   ctypes.POINTER(GsstvParams), c_void_p]),
+    "gsstv_batch_solve": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                  ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                  ctypes.POINTER(c_int)]),
+    "gsstv_batch_size": (c_int, [c_void_p]),
+    "gsstv_batch_handle": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p)]),
+    "gsstv_batch_destroy": (c_int, [c_void_p]),
     "gsstv_strerror": (ctypes.c_char_p, [c_int]),
 }
 
@@ -215,6 +224,40 @@ def gsstv_project_l1ball_noalloc(d_x: int, n: int, radius: float, d_out: int,
     _check(load().gsstv_project_l1ball_noalloc(d_x, n, radius, d_out, ctypes.byref(tau), stream or None),
            "gsstv_project_l1ball_noalloc")
     return tau.value
+
+
+def gsstv_batch_create(shapes, params, stream: int | None = None):
+    """shapes: list of (n1, n2, n3); params: list of GsstvParams (same length)."""
+    n = len(shapes)
+    arr = lambda k: (c_int * n)(*[int(sh[k]) for sh in shapes])
+    ps = (GsstvParams * n)(*params)
+    b = c_void_p()
+    _check(load().gsstv_batch_create(ctypes.byref(b), n, arr(0), arr(1), arr(2), ps, stream or None),
+           "gsstv_batch_create")
+    return b
+
+
+def gsstv_batch_solve(b, d_v, d_u, d_s=None, d_t=None) -> list:
+    """d_v, d_u, d_s, d_t: lists of device addresses (d_s, d_t may be None)."""
+    n = len(d_v)
+    vec = lambda xs: (c_void_p * n)(*xs) if xs is not None else None
+    done = (c_int * n)()
+    _check(load().gsstv_batch_solve(b, vec(d_v), vec(d_u), vec(d_s), vec(d_t), done), "gsstv_batch_solve")
+    return list(done)
+
+
+def gsstv_batch_size(b) -> int:
+    return int(load().gsstv_batch_size(b))
+
+
+def gsstv_batch_handle(b, c: int):
+    h = c_void_p()
+    _check(load().gsstv_batch_handle(b, c, ctypes.byref(h)), "gsstv_batch_handle")
+    return h
+
+
+def gsstv_batch_destroy(b):
+    _check(load().gsstv_batch_destroy(b), "gsstv_batch_destroy")
 
 
 def gsstv_strerror(code: int) -> str:

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "gsstv.h"
@@ -215,6 +216,15 @@ int run_block(gsstv_handle* h, int n) {
     return GSSTV_OK;
 }
 
+// Shapes a handle accepts: sides >= 1, N1, N2 <= 2^20, N3 <= 2^16, and six
+// stacked cubes addressable with 32-bit offsets (the stencil kernel's w
+// buffers).
+bool shape_ok(int n1, int n2, int n3) {
+    if (n1 < 1 || n2 < 1 || n3 < 1 || n1 > (1 << 20) || n2 > (1 << 20) || n3 > (1 << 16)) return false;
+    const long long cube = (long long)n3 * n1 * (((long long)n2 + 7) / 8 * 8);
+    return cube * 6 < (1ll << 32);
+}
+
 int read_scalars(gsstv_handle* h, Scal* out) {
     TRY(cuda_rc(cudaMemcpyAsync(out, h->sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st)));
     return cuda_rc(cudaStreamSynchronize(h->st));
@@ -264,7 +274,7 @@ void gsstv_default_params(gsstv_params* p) {
 int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params* p, void* stream) {
     if (!out) return GSSTV_ERR_ARG;
     *out = nullptr;
-    if (n1 < 1 || n2 < 1 || n3 < 1 || n1 > (1 << 20) || n2 > (1 << 20) || n3 > (1 << 16)) return GSSTV_ERR_ARG;
+    if (!shape_ok(n1, n2, n3)) return GSSTV_ERR_ARG;
     TRY(check_params(p));
     gsstv_handle* h = new gsstv_handle();
     h->p = *p;
@@ -273,8 +283,6 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
     h->g.n1 = n1; h->g.n2 = n2; h->g.n3 = n3;
     h->g.p2 = ((n2 + 7) / 8) * 8;
     h->g.cube = (long long)n3 * n1 * h->g.p2;
-    // the stencil kernel addresses up to six stacked cubes with 32-bit offsets
-    if (h->g.cube * 6 >= (1ll << 32)) { delete h; return GSSTV_ERR_ARG; }
     const size_t cb = (size_t)h->g.cube * h->esz;
     int rc = GSSTV_OK;
     for (int k = 0; k < 2 && rc == GSSTV_OK; ++k) {
@@ -513,6 +521,142 @@ int gsstv_project_l1ball(const float* d_x, int64_t n, double radius, float* d_ou
     if (n == 0) { if (tau_out) *tau_out = 0.0; return GSSTV_OK; }
     const int rc = l1_project_standalone(d_x, (long long)n, radius, d_out, tau_out, (cudaStream_t)stream);
     return rc == 0 ? GSSTV_OK : rc == -2 ? GSSTV_ERR_OOM : rc == -6 ? GSSTV_ERR_INTERNAL : GSSTV_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// batches of independent cubes
+// ---------------------------------------------------------------------------
+// Each cube keeps a handle of its own on a stream of its own; a solve keeps
+// one block of iterations in flight per unfinished cube (CUDA graphs, as for a
+// single handle), reads each block's scalars back asynchronously and decides
+// the cube's stopping rule (Eq. 28) on the host as gsstv_iterate does, so a
+// cube's result is the one gsstv_solve gives it alone.  Small cubes are
+// launch-bound; running many at once fills the GPU.
+struct gsstv_batch {
+    std::vector<gsstv_handle*> h;
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;
+    Scal* pinned = nullptr;        // one Scal per cube, page-locked
+    cudaStream_t caller = nullptr;
+};
+
+int gsstv_batch_destroy(gsstv_batch* b) {
+    if (!b) return GSSTV_OK;
+    for (gsstv_handle* h : b->h) gsstv_destroy(h);
+    for (cudaEvent_t e : b->ev) if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : b->st) if (s) cudaStreamDestroy(s);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    delete b;
+    return GSSTV_OK;
+}
+
+int gsstv_batch_create(gsstv_batch** out, int ncubes, const int* n1, const int* n2, const int* n3,
+                       const gsstv_params* params, void* stream) {
+    if (!out) return GSSTV_ERR_ARG;
+    *out = nullptr;
+    if (ncubes < 1 || !n1 || !n2 || !n3 || !params) return GSSTV_ERR_ARG;
+    for (int c = 0; c < ncubes; ++c) {
+        if (!shape_ok(n1[c], n2[c], n3[c])) return GSSTV_ERR_ARG;
+        TRY(check_params(&params[c]));
+    }
+    gsstv_batch* b = new gsstv_batch();
+    b->caller = (cudaStream_t)stream;
+    int rc = GSSTV_OK;
+    if (cudaMallocHost((void**)&b->pinned, sizeof(Scal) * ncubes) != cudaSuccess) {
+        b->pinned = nullptr;
+        rc = GSSTV_ERR_OOM;
+    }
+    for (int c = 0; c < ncubes && rc == GSSTV_OK; ++c) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { rc = GSSTV_ERR_CUDA; break; }
+        b->st.push_back(s);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { rc = GSSTV_ERR_CUDA; break; }
+        b->ev.push_back(e);
+        gsstv_handle* h = nullptr;
+        rc = gsstv_create(&h, n1[c], n2[c], n3[c], &params[c], s);
+        if (rc == GSSTV_OK) b->h.push_back(h);
+    }
+    if (rc != GSSTV_OK) { gsstv_batch_destroy(b); return rc; }
+    *out = b;
+    return GSSTV_OK;
+}
+
+int gsstv_batch_size(const gsstv_batch* b) { return b ? (int)b->h.size() : 0; }
+
+int gsstv_batch_solve(gsstv_batch* b, const float* const* d_v, float* const* d_u, float* const* d_s,
+                      float* const* d_t, int* iters_done) {
+    if (!b || !d_v || !d_u) return GSSTV_ERR_ARG;
+    const int nc = (int)b->h.size();
+    for (int c = 0; c < nc; ++c) if (!d_v[c] || !d_u[c]) return GSSTV_ERR_ARG;
+    // the inputs were written on the caller's stream
+    TRY(cuda_rc(cudaStreamSynchronize(b->caller)));
+    std::vector<int> done(nc, 0), left(nc, 0), busy(nc, 0), over(nc, 0);
+    int rc = GSSTV_OK;
+    auto launch_block = [&](int c) {
+        gsstv_handle* h = b->h[c];
+        const int blk = h->p.tol > 0.0 ? std::min(h->p.check_every, left[c]) : left[c];
+        TRY(run_block(h, blk));
+        left[c] -= blk;
+        done[c] += blk;
+        TRY(cuda_rc(cudaMemcpyAsync(&b->pinned[c], h->sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st)));
+        TRY(cuda_rc(cudaEventRecord(b->ev[c], h->st)));
+        busy[c] = 1;
+        return GSSTV_OK;
+    };
+    for (int c = 0; c < nc && rc == GSSTV_OK; ++c) {
+        gsstv_handle* h = b->h[c];
+        rc = gsstv_load_observation(h, d_v[c]);
+        if (rc == GSSTV_OK) rc = gsstv_reset_state(h);
+        left[c] = h->p.max_iter;
+        if (rc == GSSTV_OK) {
+            if (left[c] > 0) rc = launch_block(c);
+            else over[c] = 1;
+        }
+    }
+    int remaining = 0;
+    for (int c = 0; c < nc; ++c) remaining += over[c] ? 0 : 1;
+    while (rc == GSSTV_OK && remaining > 0) {
+        bool progress = false;
+        for (int c = 0; c < nc && rc == GSSTV_OK; ++c) {
+            if (over[c] || !busy[c]) continue;
+            const cudaError_t q = cudaEventQuery(b->ev[c]);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) { rc = GSSTV_ERR_CUDA; break; }
+            progress = true;
+            busy[c] = 0;
+            gsstv_handle* h = b->h[c];
+            const Scal& s = b->pinned[c];
+            rc = error_of(s);
+            if (rc != GSSTV_OK) break;
+            const double rel = s.u2 > 0 ? std::sqrt(s.du2 / s.u2) : INFINITY;
+            h->stats.last_rel_change = rel;
+            const bool converged = h->p.tol > 0.0 && s.u2 > 0 && rel < h->p.tol;
+            if (converged || left[c] == 0) {
+                h->stats.last_tau_s = s.ctl[0].tau;
+                h->stats.last_tau_t = s.ctl[1].tau;
+                h->stats.last_l2_scale = s.c[h->parity];
+                over[c] = 1;
+                --remaining;
+            } else {
+                rc = launch_block(c);
+            }
+        }
+        if (!progress && rc == GSSTV_OK) std::this_thread::yield();
+    }
+    for (int c = 0; c < nc && rc == GSSTV_OK; ++c) {
+        if (iters_done) iters_done[c] = done[c];
+        rc = copy_out_device(b->h[c], d_u[c], d_s ? d_s[c] : nullptr, d_t ? d_t[c] : nullptr);
+    }
+    // leave no work of the batch in flight on an error
+    for (cudaStream_t s : b->st) cudaStreamSynchronize(s);
+    return rc;
+}
+
+int gsstv_batch_handle(gsstv_batch* b, int c, gsstv_handle** out) {
+    if (!b || !out || c < 0 || c >= (int)b->h.size()) return GSSTV_ERR_ARG;
+    *out = b->h[c];
+    return GSSTV_OK;
 }
 
 const char* gsstv_strerror(int code) {

@@ -134,6 +134,59 @@ class GeoSSTVSolver:
         return B.gsstv_device_bytes(self.h)
 
 
+class GeoSSTVBatch:
+    """Independent cubes of different shapes solved together (libgsstv batch):
+    each with its own parameters and Eq. 28 stopping rule; each result equals
+    GeoSSTVSolver.solve on that cube alone."""
+
+    def __init__(self, shapes, params, stream: torch.cuda.Stream | None = None):
+        """shapes: list of (N1, N2, N3); params: one GsstvParams per cube."""
+        if not torch.cuda.is_available():
+            raise RuntimeError("GeoSSTVBatch needs a CUDA device")
+        if len(shapes) != len(params) or not shapes:
+            raise ValueError("one parameter set per cube, at least one cube")
+        B.load()
+        self.shapes = [(int(n3), int(n1), int(n2)) for n1, n2, n3 in shapes]
+        self.stream = stream or torch.cuda.current_stream()
+        self.b = B.gsstv_batch_create([tuple(s) for s in shapes], list(params), self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            B.gsstv_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, vs):
+        """vs: one contiguous float32 CUDA tensor (N3, N1, N2) per cube.
+        Returns lists u, s, t and the passes each cube ran."""
+        if len(vs) != len(self.shapes):
+            raise ValueError("one observation per cube")
+        for v, shp in zip(vs, self.shapes):
+            if tuple(v.shape) != shp or v.dtype != torch.float32 or not v.is_cuda or not v.is_contiguous():
+                raise ValueError(f"expected a contiguous float32 CUDA tensor of shape {shp}")
+        us = [torch.empty_like(v) for v in vs]
+        ss = [torch.empty_like(v) for v in vs]
+        ts = [torch.empty_like(v) for v in vs]
+        done = B.gsstv_batch_solve(self.b, [v.data_ptr() for v in vs], [u.data_ptr() for u in us],
+                                   [s.data_ptr() for s in ss], [t.data_ptr() for t in ts])
+        return us, ss, ts, done
+
+    def stats(self, c: int) -> dict:
+        s = B.gsstv_get_stats(B.gsstv_batch_handle(self.b, c))
+        return {k: getattr(s, k) for k, _ in B.GsstvStats._fields_}
+
+
 def project_l1ball(x: torch.Tensor, radius: float, out: torch.Tensor | None = None):
     """Projection of a float32 CUDA vector onto the l1 ball; returns (out, tau)."""
     if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():

@@ -70,3 +70,29 @@ def test_null_arguments(lib):
     assert lib.gsstv_iterate(None, 1, None) == B.GSSTV_ERR_ARG
     assert lib.gsstv_project_l1ball(None, 4, 1.0, None, None, None) == B.GSSTV_ERR_ARG
     assert lib.gsstv_device_bytes(None) == 0
+
+
+def test_batch_rejects_bad_arguments_before_touching_the_device(lib):
+    """The batch entry points check every cube's shape and parameters first
+    (no CUDA call is made, so this runs without a GPU)."""
+    p = B.gsstv_default_params()
+    b = ctypes.c_void_p()
+    n = (ctypes.c_int * 2)(4, 4)
+    ps = (B.GsstvParams * 2)(p, p)
+    assert lib.gsstv_batch_create(None, 2, n, n, n, ps, None) == B.GSSTV_ERR_ARG
+    assert lib.gsstv_batch_create(ctypes.byref(b), 0, n, n, n, ps, None) == B.GSSTV_ERR_ARG
+    assert lib.gsstv_batch_create(ctypes.byref(b), 2, None, n, n, ps, None) == B.GSSTV_ERR_ARG
+    bad_shape = (ctypes.c_int * 2)(4, 0)
+    assert lib.gsstv_batch_create(ctypes.byref(b), 2, n, bad_shape, n, ps, None) == B.GSSTV_ERR_ARG
+    huge = (ctypes.c_int * 2)(4, 1 << 14)
+    sides = (ctypes.c_int * 2)(4, 1 << 20)
+    assert lib.gsstv_batch_create(ctypes.byref(b), 2, sides, huge, n, ps, None) == B.GSSTV_ERR_ARG
+    q = B.gsstv_default_params()
+    q.eps = -1.0
+    bad_params = (B.GsstvParams * 2)(p, q)
+    assert lib.gsstv_batch_create(ctypes.byref(b), 2, n, n, n, bad_params, None) == B.GSSTV_ERR_ARG
+    assert not b.value
+    assert lib.gsstv_batch_solve(None, None, None, None, None, None) == B.GSSTV_ERR_ARG
+    assert lib.gsstv_batch_destroy(None) == B.GSSTV_OK
+    assert lib.gsstv_batch_size(None) == 0
+    assert lib.gsstv_batch_handle(None, 0, ctypes.byref(b)) == B.GSSTV_ERR_ARG
