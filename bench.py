@@ -503,6 +503,51 @@ def run_batch(args):
     return 0
 
 
+OMEGAS = (0.001, 0.003, 0.01, 0.03, 0.05, 0.1, 0.3, 1.0)
+
+
+def run_omega_sweep(args):
+    """MPSNR and MSSIM against the balance parameter omega for the five noise
+    cases of Sec. IV-A, radii from Eqs. 25-27, stopping rule Eq. 28 (< 1e-5, at
+    most 3000 passes); every (case, omega) problem runs in one batch.  One
+    JSON line."""
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import torch
+    from paper_2510_00562_gb300 import metrics, radii, synth
+    from paper_2510_00562_gb300.solver import GeoSSTVBatch, make_params
+    n1, n2, n3 = (int(x) for x in args.omega_sweep.split("x"))
+    problems, shapes, params, vs = [], [], [], []
+    for case in (1, 2, 3, 4, 5):
+        nz = synth.paper_case(case)
+        pb = synth.make_problem(n1, n2, n3, seed=100 + case, noise=nz)
+        r = radii.paper_radii(pb["v"], nz.sigma, nz.sp_rate, nz.stripe_rate, nz.dead_col_rate,
+                              (1 + nz.dead_width_max) / 2.0)
+        v = torch.from_numpy(pb["v"]).cuda()
+        for om in OMEGAS:
+            problems.append((case, om, pb, r))
+            shapes.append((n1, n2, n3))
+            params.append(make_params(eps=r["eps"], alpha=r["alpha"], beta=r["beta"], omega=om, tol=1e-5,
+                                      check_every=10, max_iter=3000, graph_iters=16))
+            vs.append(v)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with GeoSSTVBatch(shapes, params) as bt:
+        us, _, _, done = bt.solve(vs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    table = {}
+    for (case, om, pb, r), u, n in zip(problems, us, done):
+        un = u.cpu().numpy()
+        table.setdefault(f"case{case}", {})[str(om)] = {
+            "mpsnr_db": metrics.mpsnr(un, pb["u_bar"]),
+            "mssim_every_4th_band": metrics.mssim(un[::4], pb["u_bar"][::4]), "passes": int(n)}
+    best = {c: max(row, key=lambda k: row[k]["mpsnr_db"]) for c, row in table.items()}
+    print(json.dumps({"omega_sweep": {"cube": f"{n1}x{n2}x{n3}", "data": "synthetic", "omegas": list(OMEGAS),
+                                      "radii": "Eqs. 25-27", "solve_s": wall, "best_omega_by_mpsnr": best,
+                                      "results": table}}), flush=True)
+    return 0
+
+
 def run_precision_study(args):
     """The precision form on a cube of its own (default 1024x1024x200, 5000
     iterations: 4000 16-bit + 1000 FP32 against 5000 FP32), one JSON line."""
@@ -537,6 +582,8 @@ def main(argv=None):
     ap.add_argument("--precision-study", default=None, metavar="N1xN2xN3",
                     help="run only the mixed-vs-FP32 comparison on a cube of this size "
                          "(with --pf-iters 5000 for the 4000 + 1000 split) and print one JSON line")
+    ap.add_argument("--omega-sweep", default=None, metavar="N1xN2xN3",
+                    help="run only the omega sweep of the five noise cases on a cube of this size")
     ap.add_argument("--batch", type=int, default=0, metavar="NCUBES",
                     help="run only the batch measurement on NCUBES uneven cubes and print one JSON line")
     ap.add_argument("--shape", default="512x512x224",
@@ -551,6 +598,8 @@ def main(argv=None):
         return run_precision_study(args)
     if args.batch:
         return run_batch(args)
+    if args.omega_sweep:
+        return run_omega_sweep(args)
     return run_gpu(args)
 
 

@@ -14,9 +14,10 @@ Observation model (Eq. 14): v = u_bar + s_bar + t_bar + n, with
   every band, an offset U[-stripe_amp, stripe_amp] constant along the column
   (the noise types of Sec. IV-A, Cases 3 and 5);
 * s_bar: sparse noise -- salt-and-pepper voxels (a fraction ``sp_rate``, set to
-  0 or 1 with equal odds) and dead lines (a fraction ``dead_col_rate`` of the
-  columns in a fraction ``dead_band_rate`` of the bands, set to 0); s_bar is
-  whatever makes v hit those values, so Eq. 14 holds exactly;
+  0 or 1 with equal odds) and dead lines (in a fraction ``dead_band_rate`` of
+  the bands, a dead line starts at a fraction ``dead_col_rate`` of the columns
+  and covers a width drawn uniformly from 1..``dead_width_max`` columns, set
+  to 0); s_bar is whatever makes v hit those values, so Eq. 14 holds exactly;
 * n: Gaussian noise of standard deviation ``sigma`` on every voxel that is not
   replaced by salt-and-pepper or a dead line.
 
@@ -34,7 +35,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["NoiseSpec", "clean_cube", "make_problem", "random_state"]
+__all__ = ["NoiseSpec", "clean_cube", "make_problem", "paper_case", "random_state"]
 
 
 @dataclass
@@ -45,6 +46,22 @@ class NoiseSpec:
     stripe_amp: float = 0.25
     dead_col_rate: float = 0.0
     dead_band_rate: float = 0.0
+    dead_width_max: int = 1
+
+
+def paper_case(k: int) -> NoiseSpec:
+    """The simulated noise of Sec. IV-A, Cases 1-5: Gaussian sigma 0.1 (all
+    cases), salt-and-pepper at rate 0.05 (Cases 2, 5), vertical stripes on 5 %
+    of the columns with intensity U[-0.5, 0.5] (Cases 3, 5), dead lines
+    starting at 1 % of the columns with widths 1-3 (Cases 4, 5).  Reading: the
+    stripes and dead lines affect every band."""
+    sp = 0.05 if k in (2, 5) else 0.0
+    st = 0.05 if k in (3, 5) else 0.0
+    dl = 0.01 if k in (4, 5) else 0.0
+    if k not in (1, 2, 3, 4, 5):
+        raise ValueError("cases 1..5")
+    return NoiseSpec(sigma=0.1, sp_rate=sp, stripe_rate=st, stripe_amp=0.5,
+                     dead_col_rate=dl, dead_band_rate=1.0 if dl else 0.0, dead_width_max=3)
 
 
 def clean_cube(n1: int, n2: int, n3: int, rng: np.random.Generator, n_regions: int = 6):
@@ -95,6 +112,15 @@ def make_problem(n1: int, n2: int, n3: int, seed: int = 0, noise: NoiseSpec | No
     # dead lines: zeroed columns in a subset of bands
     dead_bands = rng.uniform(size=n3) < noise.dead_band_rate
     dead_cols = (rng.uniform(size=(n3, n2)) < noise.dead_col_rate) & dead_bands[:, None]
+    if noise.dead_width_max > 1:
+        # each start covers 1..dead_width_max columns (drawn only when widths
+        # above 1 are asked for, so the other workloads keep their bytes)
+        width = rng.integers(1, noise.dead_width_max + 1, size=(n3, n2))
+        starts = dead_cols
+        dead_cols = np.zeros_like(starts)
+        for w in range(noise.dead_width_max):
+            sh = starts & (width > w)
+            dead_cols[:, w:] |= sh[:, :n2 - w] if w else sh
     dead = np.broadcast_to(dead_cols[:, None, :], shape)
 
     gauss = rng.standard_normal(size=shape, dtype=np.float32) * np.float32(noise.sigma)
