@@ -34,18 +34,27 @@ struct WinInfo {
 // n_hi, s_hi: count and sum of |x| > theta_hi; cand[0..m_raw): every |x| in
 // (theta_lo, theta_hi].  Returns 0 with *tau_out; 2 when the root lies above
 // the window; 1 when it lies below or the candidates overflowed the buffer.
+// stage (optional): shared memory for stage_cap floats that the block no
+// longer uses; when the candidates fit they are copied there on the first
+// pass and every later pass reads them from it instead of from L2.
 static __device__ int l1_window_finish(double n_hi, double s_hi, const float* cand, unsigned m_raw,
                                        double theta_lo, double theta_hi, double r,
                                        double* tau_out, double* red_d,
-                                       unsigned long long* red_u, WinInfo* info = nullptr) {
+                                       unsigned long long* red_u, WinInfo* info = nullptr,
+                                       float* stage = nullptr, unsigned stage_cap = 0) {
     const double phi_hi = s_hi - n_hi * theta_hi - r;
     if (info) info->phi_hi = phi_hi;
     if (m_raw > kCandCap) return 1;
     const unsigned m = m_raw;
     if (phi_hi > 0.0) return 2;                        // root above the window
+    const bool staged = stage && m <= stage_cap;
     Kahan ks;
-    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) ks.add(__ldcg(cand + k));
-    const double sum_c = block_sum(ks.value(), red_d);
+    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+        const float x = __ldcg(cand + k);
+        if (staged) stage[k] = x;
+        ks.add(x);
+    }
+    const double sum_c = block_sum(ks.value(), red_d);      // (its barriers publish the stage)
     const double n_all = n_hi + (double)m;
     const double phi_lo = s_hi + sum_c - n_all * theta_lo - r;
     if (info) { info->phi_lo = phi_lo; info->n_lo = n_all; }
@@ -62,7 +71,7 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
         Kahan ka;
         unsigned long long c = 0;
         for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-            const float x = __ldcg(cand + k);
+            const float x = staged ? stage[k] : __ldcg(cand + k);
             if (x > tf) { ka.add(x); ++c; }
         }
         const double sa = block_sum(ka.value(), red_d);

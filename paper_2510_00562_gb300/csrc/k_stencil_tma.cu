@@ -666,7 +666,9 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
         const double tlo = C.theta_lo, thi = C.theta_hi;
         double tau = 0.0;
         WinInfo wi;
-        const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi);
+        // the tile's shared memory (up to the mbarriers) is idle now: stage the candidates there
+        const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi,
+                                          reinterpret_cast<float*>(sm), L::OFF_BAR / 4);
         if (tid == 0) {
             if (!miss) {
                 l1_record_tau(C, tau, (double)min(m, kCandCap), thi - tlo, true);
