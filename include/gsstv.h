@@ -190,6 +190,48 @@ int gsstv_batch_handle(gsstv_batch* b, int c, gsstv_handle** out);
 /* Releases the batch and every solver in it.  NULL is accepted. */
 int gsstv_batch_destroy(gsstv_batch* b);
 
+/* ---- reverse mode (gradients of the unrolled iteration) -------------------
+ * The derivative of K passes of Algorithm 1 with respect to the observation
+ * v and the radii and weight (eps, alpha, beta, omega), for learning them or
+ * for sensitivity studies.  The iteration's operators are piecewise smooth;
+ * the transpose uses the derivatives that hold almost everywhere: the box
+ * (Eq. 21) passes where mu_lo < u+ < mu_hi; the group soft-threshold (Eq. 24)
+ * above its threshold has Jacobian (1 - g/|x|) I + g x x^T/|x|^3; the
+ * l1-ball projection (Sec. III-B), when active, keeps the support A of its
+ * result and removes the mean of sign(x) p over A (its derivative in the
+ * radius is that mean); the l2-ball step (Eq. 23, through Eq. 3) is
+ * y4 = (1 - c) q with Jacobian I - (eps g/|q|)(I - q^ q^^T) when the ball is
+ * active.  The linear operators D, D_s, L are transposed exactly.  Float32
+ * arithmetic throughout; only handles with GSSTV_FP32 storage are accepted
+ * (GSSTV_ERR_ARG otherwise).
+ *
+ * gsstv_vjp_step: one pass.  x: the state before the pass, x_next: the state
+ * after it (as gsstv_iterate(h, 1) gives it from x with the handle's loaded
+ * observation and parameters), bar_next: the adjoint of x_next; writes the
+ * adjoint of x to bar (bar may be bar_next itself: the transpose runs in
+ * place; no other views may overlap).  Adds the adjoint of v to d_vbar (N
+ * floats) and those of (eps, alpha, beta, omega) to h_pbar[0..3] (host).
+ * All views: float32 device arrays in the layout of gsstv_state_view.  Uses
+ * a workspace of about 16 N floats held by the handle from the first call;
+ * synchronises the stream.
+ *
+ * gsstv_unrolled_vjp: `iters` passes from the standard start (u = v, the
+ * rest zero; the observation loaded in the handle, tol ignored) and back.
+ * d_ubar: adjoint of u after the last pass (N floats, device).  Writes to
+ * d_vbar (N floats, device) the adjoint of v -- through every pass and the
+ * start u = v -- and to h_pbar[0..3] those of eps, alpha, beta, omega.
+ * ckpt_every: passes between checkpoints (0 = ceil(sqrt(iters))); with
+ * C = min(ckpt_every, iters) the call allocates ceil(iters/C) + C + 1 states
+ * of 21 N floats and a 16 N-float workspace with cudaMalloc and frees them
+ * before returning (GSSTV_ERR_OOM if they do not fit), runs the passes about
+ * twice in all, and leaves the handle's state unspecified (reset it before
+ * iterating again).  Synchronises the stream. */
+int gsstv_vjp_step(gsstv_handle* h, const gsstv_state_view* x, const gsstv_state_view* x_next,
+                   const gsstv_state_view* bar_next, const gsstv_state_view* bar, float* d_vbar,
+                   double* h_pbar);
+int gsstv_unrolled_vjp(gsstv_handle* h, int iters, int ckpt_every, const float* d_ubar, float* d_vbar,
+                       double* h_pbar);
+
 /* Projection onto the l1 ball {z : ||z||_1 <= radius} (Sec. III-B, the prox
  * of the indicator of B_{1,alpha}): d_out = sign(x) max(|x| - tau, 0), with
  * tau >= 0 the root of sum max(|x_i| - tau, 0) = radius, or d_out = d_x when

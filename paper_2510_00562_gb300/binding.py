@@ -86,6 +86,9 @@ _SIGS = {
     "gsstv_batch_size": (c_int, [c_void_p]),
     "gsstv_batch_handle": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p)]),
     "gsstv_batch_destroy": (c_int, [c_void_p]),
+    "gsstv_vjp_step": (c_int, [c_void_p] + [ctypes.POINTER(GsstvStateView)] * 4 +
+                       [c_void_p, ctypes.POINTER(c_double)]),
+    "gsstv_unrolled_vjp": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
     "gsstv_strerror": (ctypes.c_char_p, [c_int]),
 }
 
@@ -258,6 +261,23 @@ def gsstv_batch_handle(b, c: int):
 
 def gsstv_batch_destroy(b):
     _check(load().gsstv_batch_destroy(b), "gsstv_batch_destroy")
+
+
+def gsstv_vjp_step(h, x: dict, x_next: dict, bar_next: dict, bar: dict, d_vbar: int, pbar=None) -> list:
+    """One pass transposed; x, x_next, bar_next, bar: dicts of device
+    addresses.  Adds to d_vbar and to pbar (4 floats, returned as a list)."""
+    acc = (c_double * 4)(*(pbar or [0.0] * 4))
+    vs = [_view(d) for d in (x, x_next, bar_next, bar)]
+    _check(load().gsstv_vjp_step(h, *[ctypes.byref(v) for v in vs], d_vbar, acc), "gsstv_vjp_step")
+    return list(acc)
+
+
+def gsstv_unrolled_vjp(h, iters: int, ckpt_every: int, d_ubar: int, d_vbar: int) -> list:
+    """Adjoint of `iters` passes from the standard start; returns the adjoints
+    of (eps, alpha, beta, omega)."""
+    acc = (c_double * 4)()
+    _check(load().gsstv_unrolled_vjp(h, iters, ckpt_every, d_ubar, d_vbar, acc), "gsstv_unrolled_vjp")
+    return list(acc)
 
 
 def gsstv_strerror(code: int) -> str:

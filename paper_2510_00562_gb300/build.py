@@ -23,7 +23,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgsstv.so")
-SOURCES = ["gsstv.cu", "k_stencil.cu", "k_stencil_tma.cu", "k_light.cu"]
+SOURCES = ["gsstv.cu", "k_stencil.cu", "k_stencil_tma.cu", "k_light.cu", "k_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

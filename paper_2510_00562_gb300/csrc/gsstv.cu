@@ -34,6 +34,7 @@ struct gsstv_handle {
     void *w1[2]{}, *w2[2]{}, *y1[2]{}, *y2[2]{};
     float* v = nullptr;
     float* tmp = nullptr;         // dense float32 scratch for host copies (16-bit storage)
+    void* adj_work = nullptr;     // scratch of gsstv_vjp_step (allocated on first use)
     Scal* sc = nullptr;
     L1Work l1{};
     double* k2_part = nullptr;
@@ -409,6 +410,24 @@ int gsstv_iterate(gsstv_handle* h, int n, int* iters_done) {
     return GSSTV_OK;
 }
 
+static bool view_ok(const gsstv_state_view* v) {
+    return v && v->u && v->s && v->t && v->w1 && v->w2 && v->y1 && v->y2 && v->y3 && v->y4;
+}
+
+// Unpacks the current state into float32 views on the handle's stream (no sync).
+static int enqueue_get_state(gsstv_handle* h, const gsstv_state_view* v) {
+    const int par = h->parity, sto = h->p.storage;
+    TRY(map_launch(launch_unpack(sto, h->u[par], v->u, h->g, 1, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->s[par], v->s, h->g, 1, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->t[par], v->t, h->g, 1, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->w1[par], v->w1, h->g, 6, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->w2[par], v->w2, h->g, 6, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->y1[par], v->y1, h->g, 2, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->y2[par], v->y2, h->g, 2, h->st)));
+    TRY(map_launch(launch_unpack(sto, h->y3[par], v->y3, h->g, 1, h->st)));
+    return map_launch(launch_scale_unpack(sto, h->q[par], &h->sc->c[par], v->y4, h->g, h->st));
+}
+
 static int copy_out_device(gsstv_handle* h, float* d_u, float* d_s, float* d_t) {
     const int par = h->parity;
     if (d_u) TRY(map_launch(launch_unpack(h->p.storage, h->u[par], d_u, h->g, 1, h->st)));
@@ -453,24 +472,13 @@ int gsstv_solve_host(gsstv_handle* h, const float* h_v, float* h_u, float* h_s, 
 }
 
 int gsstv_get_state(gsstv_handle* h, const gsstv_state_view* v) {
-    if (!h || !v || !v->u || !v->s || !v->t || !v->w1 || !v->w2 || !v->y1 || !v->y2 || !v->y3 || !v->y4)
-        return GSSTV_ERR_ARG;
-    const int par = h->parity, sto = h->p.storage;
-    TRY(map_launch(launch_unpack(sto, h->u[par], v->u, h->g, 1, h->st)));
-    TRY(map_launch(launch_unpack(sto, h->s[par], v->s, h->g, 1, h->st)));
-    TRY(map_launch(launch_unpack(sto, h->t[par], v->t, h->g, 1, h->st)));
-    TRY(map_launch(launch_unpack(sto, h->w1[par], v->w1, h->g, 6, h->st)));
-    TRY(map_launch(launch_unpack(sto, h->w2[par], v->w2, h->g, 6, h->st)));
-    TRY(map_launch(launch_unpack(sto, h->y1[par], v->y1, h->g, 2, h->st)));
-    TRY(map_launch(launch_unpack(sto, h->y2[par], v->y2, h->g, 2, h->st)));
-    TRY(map_launch(launch_unpack(sto, h->y3[par], v->y3, h->g, 1, h->st)));
-    TRY(map_launch(launch_scale_unpack(sto, h->q[par], &h->sc->c[par], v->y4, h->g, h->st)));
+    if (!h || !view_ok(v)) return GSSTV_ERR_ARG;
+    TRY(enqueue_get_state(h, v));
     return cuda_rc(cudaStreamSynchronize(h->st));
 }
 
 int gsstv_set_state(gsstv_handle* h, const gsstv_state_view* v) {
-    if (!h || !v || !v->u || !v->s || !v->t || !v->w1 || !v->w2 || !v->y1 || !v->y2 || !v->y3 || !v->y4)
-        return GSSTV_ERR_ARG;
+    if (!h || !view_ok(v)) return GSSTV_ERR_ARG;
     const int par = h->parity, sto = h->p.storage;
     TRY(map_launch(launch_pack(sto, v->u, h->u[par], h->g, 1, h->st)));
     TRY(map_launch(launch_pack(sto, v->s, h->s[par], h->g, 1, h->st)));
@@ -521,6 +529,143 @@ int gsstv_project_l1ball(const float* d_x, int64_t n, double radius, float* d_ou
     if (n == 0) { if (tau_out) *tau_out = 0.0; return GSSTV_OK; }
     const int rc = l1_project_standalone(d_x, (long long)n, radius, d_out, tau_out, (cudaStream_t)stream);
     return rc == 0 ? GSSTV_OK : rc == -2 ? GSSTV_ERR_OOM : rc == -6 ? GSSTV_ERR_INTERNAL : GSSTV_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// reverse mode: vector-Jacobian products of the iteration
+// ---------------------------------------------------------------------------
+// One pass transposed (gsstv_vjp_step) and the adjoint of a whole run of K
+// passes from the standard start (gsstv_unrolled_vjp): the forward run keeps
+// a checkpoint every C passes, the reverse sweep re-runs each segment from
+// its checkpoint, keeps that segment's states and applies the one-pass
+// transpose to them from the last to the first.
+namespace {
+
+constexpr int kStateCubes = 21;   // u, s, t, w1 (6), w2 (6), y1 (2), y2 (2), y3, y4
+
+gsstv_state_view state_at(float* base, long long n) {
+    gsstv_state_view v;
+    v.u = base; v.s = base + n; v.t = base + 2 * n; v.w1 = base + 3 * n; v.w2 = base + 9 * n;
+    v.y1 = base + 15 * n; v.y2 = base + 17 * n; v.y3 = base + 19 * n; v.y4 = base + 20 * n;
+    return v;
+}
+
+void view_ptrs(const gsstv_state_view* v, float* out[9]) {
+    out[0] = v->u; out[1] = v->s; out[2] = v->t; out[3] = v->w1; out[4] = v->w2;
+    out[5] = v->y1; out[6] = v->y2; out[7] = v->y3; out[8] = v->y4;
+}
+
+int vjp_launch(gsstv_handle* h, const gsstv_state_view* x, const gsstv_state_view* x1,
+               const gsstv_state_view* b1, const gsstv_state_view* bo, float* vbar, double* d_pbar,
+               void* work) {
+    const gsstv_params& p = h->p;
+    const double prm[16] = {p.gamma_u, p.gamma_w1, p.gamma_w2, p.gamma_s, p.gamma_t,
+                            p.gamma_y1, p.gamma_y2, p.gamma_y3, p.gamma_y4,
+                            p.gamma_w1 * p.omega, p.gamma_w2, p.mu_lo, p.mu_hi, p.eps, p.alpha, p.beta};
+    float *xa[9], *x1a[9], *b1a[9], *boa[9];
+    view_ptrs(x, xa); view_ptrs(x1, x1a); view_ptrs(b1, b1a); view_ptrs(bo, boa);
+    const Geom& g = h->g;
+    return map_launch(launch_adjoint_step(g.n1, g.n2, g.n3, xa, x1a, b1a, boa, h->v, g.p2, vbar, d_pbar,
+                                          work, prm, h->st));
+}
+
+// device scratch of one gsstv_unrolled_vjp call, released on every return
+struct Scratch {
+    void* p = nullptr;
+    ~Scratch() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+int gsstv_vjp_step(gsstv_handle* h, const gsstv_state_view* x, const gsstv_state_view* x_next,
+                   const gsstv_state_view* bar_next, const gsstv_state_view* bar, float* d_vbar,
+                   double* h_pbar) {
+    if (!h || !view_ok(x) || !view_ok(x_next) || !view_ok(bar_next) || !view_ok(bar) || !d_vbar || !h_pbar)
+        return GSSTV_ERR_ARG;
+    if (h->p.storage != GSSTV_FP32) return GSSTV_ERR_ARG;
+    const long long n = (long long)h->g.n1 * h->g.n2 * h->g.n3;
+    const size_t wb = adjoint_workspace_bytes(n);
+    if (!h->adj_work) TRY(dalloc(h, &h->adj_work, wb + 4 * sizeof(double)));
+    double* d_pbar = (double*)((char*)h->adj_work + wb);
+    TRY(cuda_rc(cudaMemsetAsync(d_pbar, 0, 4 * sizeof(double), h->st)));
+    TRY(vjp_launch(h, x, x_next, bar_next, bar, d_vbar, d_pbar, h->adj_work));
+    double pb[4];
+    TRY(cuda_rc(cudaMemcpyAsync(pb, d_pbar, sizeof(pb), cudaMemcpyDeviceToHost, h->st)));
+    TRY(cuda_rc(cudaStreamSynchronize(h->st)));
+    for (int k = 0; k < 4; ++k) h_pbar[k] += pb[k];
+    return GSSTV_OK;
+}
+
+int gsstv_unrolled_vjp(gsstv_handle* h, int iters, int ckpt_every, const float* d_ubar, float* d_vbar,
+                       double* h_pbar) {
+    if (!h || iters < 0 || ckpt_every < 0 || !d_ubar || !d_vbar || !h_pbar) return GSSTV_ERR_ARG;
+    if (h->p.storage != GSSTV_FP32) return GSSTV_ERR_ARG;
+    const long long n = (long long)h->g.n1 * h->g.n2 * h->g.n3;
+    const size_t cube = (size_t)n * sizeof(float);
+    for (int k = 0; k < 4; ++k) h_pbar[k] = 0.0;
+    if (iters == 0) {   // u_0 = v
+        TRY(cuda_rc(cudaMemcpyAsync(d_vbar, d_ubar, cube, cudaMemcpyDeviceToDevice, h->st)));
+        return cuda_rc(cudaStreamSynchronize(h->st));
+    }
+    const int C = ckpt_every > 0 ? std::min(ckpt_every, iters)
+                                 : std::max(1, (int)std::ceil(std::sqrt((double)iters)));
+    const int nck = (iters + C - 1) / C;
+    const size_t sbytes = kStateCubes * cube;
+    const size_t wb = adjoint_workspace_bytes(n);
+    // nck checkpoints, C segment states, the adjoint state, the workspace
+    Scratch scr;
+    if (cudaMalloc(&scr.p, (size_t)(nck + C + 1) * sbytes + wb + 4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        scr.p = nullptr;
+        return GSSTV_ERR_OOM;
+    }
+    float* base = (float*)scr.p;
+    auto slot = [&](int k) { return state_at(base + (size_t)k * kStateCubes * n, n); };
+    const gsstv_state_view bar = slot(nck + C);
+    void* work = base + (size_t)(nck + C + 1) * kStateCubes * n;
+    double* d_pbar = (double*)((char*)work + wb);
+    // forward: the state at the start of every segment (the last segment
+    // needs no run here)
+    TRY(gsstv_reset_state(h));
+    for (int c = 0; c < nck; ++c) {
+        const gsstv_state_view v = slot(c);
+        TRY(enqueue_get_state(h, &v));
+        if (c + 1 < nck) TRY(run_block(h, C));
+    }
+    TRY(flush_timing(h));
+    Scal sc;
+    TRY(read_scalars(h, &sc));
+    TRY(error_of(sc));
+    // reverse sweep, the adjoint transposed in place
+    TRY(cuda_rc(cudaMemsetAsync(bar.u, 0, sbytes, h->st)));
+    TRY(cuda_rc(cudaMemcpyAsync(bar.u, d_ubar, cube, cudaMemcpyDeviceToDevice, h->st)));
+    TRY(cuda_rc(cudaMemsetAsync(d_vbar, 0, cube, h->st)));
+    TRY(cuda_rc(cudaMemsetAsync(d_pbar, 0, 4 * sizeof(double), h->st)));
+    for (int c = nck - 1; c >= 0; --c) {
+        const int len = std::min(C, iters - c * C);
+        const gsstv_state_view start = slot(c);
+        TRY(gsstv_set_state(h, &start));
+        for (int j = 1; j <= len; ++j) {             // segment state j in slot nck + j - 1
+            TRY(run_block(h, 1));
+            const gsstv_state_view v = slot(nck + j - 1);
+            TRY(enqueue_get_state(h, &v));
+        }
+        TRY(flush_timing(h));
+        TRY(read_scalars(h, &sc));
+        TRY(error_of(sc));
+        for (int j = len - 1; j >= 0; --j) {
+            const gsstv_state_view xj = j == 0 ? start : slot(nck + j - 1);
+            const gsstv_state_view xj1 = slot(nck + j);
+            TRY(vjp_launch(h, &xj, &xj1, &bar, &bar, d_vbar, d_pbar, work));
+        }
+    }
+    // the start u = v
+    TRY(map_launch(launch_axpy(d_vbar, bar.u, 1.0f, n, h->st)));
+    double pb[4];
+    TRY(cuda_rc(cudaMemcpyAsync(pb, d_pbar, sizeof(pb), cudaMemcpyDeviceToHost, h->st)));
+    TRY(cuda_rc(cudaStreamSynchronize(h->st)));
+    for (int k = 0; k < 4; ++k) h_pbar[k] = pb[k];
+    return GSSTV_OK;
 }
 
 // ---------------------------------------------------------------------------

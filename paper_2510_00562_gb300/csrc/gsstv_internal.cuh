@@ -315,6 +315,19 @@ int launch_unpack(int storage, const void* src, float* dst, const Geom& g, int n
 int launch_scale_unpack(int storage, const void* q, const double* c, float* dst, const Geom& g,
                         cudaStream_t st);
 
+// reverse mode of one pass on dense float32 states (k_adjoint.cu).  x, x1:
+// states k and k+1 (u, s, t, w1, w2, y1, y2, y3, y4); b1: adjoint of state
+// k+1; bo: adjoint of state k (may be b1 itself); v with row pitch v_pitch;
+// vbar += the adjoint of v; pbar[0..3] += those of eps, alpha, beta, omega.
+// prm: g_u, g_w1, g_w2, g_s, g_t, g_y1..g_y4, thr_w1, thr_w2, mu_lo, mu_hi,
+// eps, alpha, beta.  work: adjoint_workspace_bytes(N) bytes.
+size_t adjoint_workspace_bytes(long long n);
+int launch_adjoint_step(int n1, int n2, int n3, const float* const x[9], const float* const x1[9],
+                        const float* const b1[9], float* const bo[9], const float* v, int v_pitch,
+                        float* vbar, double* pbar, void* work, const double prm[16], cudaStream_t st);
+// y += a x on n floats
+int launch_axpy(float* y, const float* x, float a, long long n, cudaStream_t st);
+
 // standalone projection
 int l1_project_standalone(const float* x, long long n, double radius, float* out, double* tau,
                           cudaStream_t st);

@@ -14,6 +14,8 @@ STORAGE = {"fp32": B.GSSTV_FP32, "bf16": B.GSSTV_BF16, "fp16": B.GSSTV_FP16}
 STATE_KEYS = ("u", "s", "t", "w1", "w2", "y1", "y2", "y3", "y4")
 STATE_LEAD = {"u": (), "s": (), "t": (), "w1": (3, 2), "w2": (3, 2), "y1": (2,), "y2": (2,),
               "y3": (), "y4": ()}
+# the parameters the reverse mode differentiates, in the order of the C ABI
+GRAD_PARAMS = ("eps", "alpha", "beta", "omega")
 
 
 def make_params(**kw) -> B.GsstvParams:
@@ -119,6 +121,28 @@ class GeoSSTVSolver:
     def set_state(self, st: dict):
         tens = {k: self._dev(st[k], STATE_LEAD[k]) for k in STATE_KEYS}
         B.gsstv_set_state(self.h, {k: v.data_ptr() for k, v in tens.items()})
+
+    def vjp_step(self, x: dict, x_next: dict, bar_next: dict, vbar: torch.Tensor | None = None,
+                 in_place: bool = False):
+        """Transpose of one pass (gsstv_vjp_step): x the state before it,
+        x_next the state after it, bar_next the adjoint of x_next.  Returns
+        (adjoint of x, adjoint of v, adjoints of eps/alpha/beta/omega); vbar,
+        if given, is accumulated into; in_place reuses bar_next's buffers."""
+        views = [{k: self._dev(d[k], STATE_LEAD[k]) for k in STATE_KEYS} for d in (x, x_next, bar_next)]
+        bar = views[2] if in_place else {k: self._empty(STATE_LEAD[k]) for k in STATE_KEYS}
+        vbar = torch.zeros(self.shape, dtype=torch.float32, device="cuda") if vbar is None else self._dev(vbar)
+        ptr = lambda d: {k: t.data_ptr() for k, t in d.items()}
+        pb = B.gsstv_vjp_step(self.h, ptr(views[0]), ptr(views[1]), ptr(views[2]), ptr(bar), vbar.data_ptr())
+        return bar, vbar, dict(zip(GRAD_PARAMS, pb))
+
+    def unrolled_vjp(self, iters: int, ubar: torch.Tensor, ckpt_every: int = 0):
+        """Adjoint of `iters` passes from the standard start on the loaded
+        observation (gsstv_unrolled_vjp): ubar is the adjoint of u after the
+        last pass; returns (adjoint of v, adjoints of eps/alpha/beta/omega)."""
+        vbar = self._empty()
+        pb = B.gsstv_unrolled_vjp(self.h, int(iters), int(ckpt_every), self._dev(ubar).data_ptr(),
+                                  vbar.data_ptr())
+        return vbar, dict(zip(GRAD_PARAMS, pb))
 
     def stats(self) -> dict:
         s = B.gsstv_get_stats(self.h)
