@@ -567,6 +567,110 @@ def run_precision_study(args):
     return 0
 
 
+# words per voxel of one transposed pass in place (k_adjoint.cu), every array
+# element read or written once per kernel: SUMS reads 10; CUBE reads 18
+# (states k and k+1 where q and the box need them, the adjoints of u, s, t,
+# y1..y4, v, v_bar) and writes 8; AUX reads 32 (w1, w2 and their adjoints,
+# y1, y2 and theirs) and writes 24; FIN1 reads 9 and writes 4; FIN2 reads
+# 17 and writes 4.
+ADJ_WORDS = 126
+
+
+def run_grad(args):
+    """Reverse mode at one size: K passes forward (gsstv_solve) against the
+    gradient of the MSE loss of u_K with respect to v and (eps, alpha, beta,
+    omega) (gsstv_unrolled_vjp), central finite differences of the loss
+    (step 1e-3 relative) beside the parameter gradients and one directional
+    derivative in v, and the transposed pass alone against the HBM roofline.
+    One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2510_00562_gb300 import synth
+    from paper_2510_00562_gb300.solver import GRAD_PARAMS, GeoSSTVSolver, make_params
+    n1, n2, n3 = (int(x) for x in args.grad.split("x"))
+    K, C = args.grad_iters, args.grad_ckpt
+    N = n1 * n2 * n3
+    pb = synth.make_problem(n1, n2, n3, seed=0, noise=synth.NoiseSpec(**NOISE))
+    v = torch.from_numpy(pb["v"]).cuda()
+    ub = torch.from_numpy(pb["u_bar"].astype("float32")).cuda()
+    stream = torch.cuda.current_stream()
+    peak, src = measured_peaks()
+    prm = dict(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03)
+
+    def ev_time(fn, r):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(r):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / r
+
+    with GeoSSTVSolver(n1, n2, n3, make_params(max_iter=K, graph_iters=16, **prm), stream=stream) as sol:
+        def loss_of(vv, **over):
+            sol.set_params(**{**prm, **over})
+            u_, _, _, _ = sol.solve(vv)
+            return float(((u_.double() - ub.double()) ** 2).mean()), u_
+
+        loss, u = loss_of(v)
+        seed = (2.0 / N) * (u - ub)
+        fwd_ms = ev_time(lambda: sol.solve(v), 3)
+
+        def bwd():
+            sol.load(v)
+            return sol.unrolled_vjp(K, seed, ckpt_every=C)
+
+        vbar, pbar = bwd()
+        bwd_ms = ev_time(bwd, 3)
+        free0, _ = torch.cuda.mem_get_info()
+        scratch = ((K + C - 1) // C + C + 1) * 21 * N * 4 + 15 * N * 4 + 160
+        # central differences, step 1e-3 of each parameter
+        fd = {}
+        for k in GRAD_PARAMS:
+            h = 1e-3 * prm[k]
+            lp, _ = loss_of(v, **{k: prm[k] + h})
+            lm, _ = loss_of(v, **{k: prm[k] - h})
+            fd[k] = {"fd": (lp - lm) / (2 * h), "adjoint": pbar[k]}
+        # one direction in v, zero on the salt-and-pepper voxels (0 or 1
+        # exactly: the box's kinks, where only one-sided derivatives exist)
+        g = torch.from_numpy(np.random.default_rng(1).standard_normal(pb["v"].shape).astype("float32")).cuda()
+        g = torch.where((v == 0) | (v == 1), torch.zeros_like(g), g)
+        hv = 1e-3 * float(v.abs().mean())
+        lp, _ = loss_of((v + hv * g).contiguous())
+        lm, _ = loss_of((v - hv * g).contiguous())
+        fd["v_direction"] = {"fd": (lp - lm) / (2 * hv), "adjoint": float((vbar.double() * g.double()).sum())}
+        for ent in fd.values():
+            ent["rel_diff"] = abs(ent["fd"] - ent["adjoint"]) / max(abs(ent["fd"]), 1e-300)
+        sol.set_params(**prm)
+        # the transposed pass alone, in place, no parameter read-back
+        sol.load(v)
+        sol.iterate(5)
+        x = sol.get_state()
+        sol.iterate(1)
+        x1 = sol.get_state()
+        bar = {k: 1e-3 * torch.randn_like(t) for k, t in x.items()}
+        vb = torch.zeros_like(v)
+        for _ in range(3):
+            sol.vjp_step(x, x1, bar, vbar=vb, in_place=True, want_params=False)
+        step_ms = ev_time(lambda: sol.vjp_step(x, x1, bar, vbar=vb, in_place=True, want_params=False), 20)
+        handle_bytes = sol.device_bytes()
+    ach = ADJ_WORDS * 4 * N / (step_ms * 1e-3) / 1e9
+    line = {"grad": {
+        "cube": f"{n1}x{n2}x{n3}", "passes": K, "data": "synthetic", "noise": NOISE,
+        "loss": "mean((u_K - u_bar)^2)", "loss_value": loss,
+        "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
+        "checkpoint_every": C, "scratch_bytes": scratch, "handle_bytes": handle_bytes,
+        "free_bytes_after_backward": free0,
+        "gradients_vs_central_differences": fd,
+        "adjoint_pass": {"ms": step_ms, "kernels": 5, "algorithmic_bytes_per_voxel": ADJ_WORDS * 4,
+                         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                      "frac": ach / peak, "peak_source": src}},
+        "unit": "ms"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -586,6 +690,10 @@ def main(argv=None):
                     help="run only the omega sweep of the five noise cases on a cube of this size")
     ap.add_argument("--batch", type=int, default=0, metavar="NCUBES",
                     help="run only the batch measurement on NCUBES uneven cubes and print one JSON line")
+    ap.add_argument("--grad", default=None, metavar="N1xN2xN3",
+                    help="run only the reverse-mode measurement on a cube of this size")
+    ap.add_argument("--grad-iters", type=int, default=200)
+    ap.add_argument("--grad-ckpt", type=int, default=20, help="passes between checkpoints")
     ap.add_argument("--shape", default="512x512x224",
                     help="N1xN2xN3; anything but the default is a profiling case, not a bench line")
     args = ap.parse_args(argv)
@@ -600,6 +708,8 @@ def main(argv=None):
         return run_batch(args)
     if args.omega_sweep:
         return run_omega_sweep(args)
+    if args.grad:
+        return run_grad(args)
     return run_gpu(args)
 
 

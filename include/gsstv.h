@@ -212,8 +212,9 @@ int gsstv_batch_destroy(gsstv_batch* b);
  * place; no other views may overlap).  Adds the adjoint of v to d_vbar (N
  * floats) and those of (eps, alpha, beta, omega) to h_pbar[0..3] (host).
  * All views: float32 device arrays in the layout of gsstv_state_view.  Uses
- * a workspace of about 16 N floats held by the handle from the first call;
- * synchronises the stream.
+ * a workspace of about 16 N floats held by the handle from the first call.
+ * Synchronises the stream to read the parameter adjoints back; with h_pbar
+ * NULL it skips them and returns once the work is queued.
  *
  * gsstv_unrolled_vjp: `iters` passes from the standard start (u = v, the
  * rest zero; the observation loaded in the handle, tol ignored) and back.

@@ -263,13 +263,16 @@ def gsstv_batch_destroy(b):
     _check(load().gsstv_batch_destroy(b), "gsstv_batch_destroy")
 
 
-def gsstv_vjp_step(h, x: dict, x_next: dict, bar_next: dict, bar: dict, d_vbar: int, pbar=None) -> list:
+def gsstv_vjp_step(h, x: dict, x_next: dict, bar_next: dict, bar: dict, d_vbar: int, pbar=None,
+                   want_params: bool = True):
     """One pass transposed; x, x_next, bar_next, bar: dicts of device
-    addresses.  Adds to d_vbar and to pbar (4 floats, returned as a list)."""
-    acc = (c_double * 4)(*(pbar or [0.0] * 4))
+    addresses.  Adds to d_vbar and to pbar (4 floats, returned as a list);
+    want_params=False passes NULL (no parameter adjoints, no synchronisation)
+    and returns None."""
+    acc = (c_double * 4)(*(pbar or [0.0] * 4)) if want_params else None
     vs = [_view(d) for d in (x, x_next, bar_next, bar)]
     _check(load().gsstv_vjp_step(h, *[ctypes.byref(v) for v in vs], d_vbar, acc), "gsstv_vjp_step")
-    return list(acc)
+    return list(acc) if want_params else None
 
 
 def gsstv_unrolled_vjp(h, iters: int, ckpt_every: int, d_ubar: int, d_vbar: int) -> list:

@@ -543,10 +543,12 @@ namespace {
 
 constexpr int kStateCubes = 21;   // u, s, t, w1 (6), w2 (6), y1 (2), y2 (2), y3, y4
 
-gsstv_state_view state_at(float* base, long long n) {
+// views into one state of kStateCubes * P floats (P = adj_stride(N): every
+// field on a 256-byte boundary; the planes of w1, w2, y1, y2 at stride N)
+gsstv_state_view state_at(float* base, long long P) {
     gsstv_state_view v;
-    v.u = base; v.s = base + n; v.t = base + 2 * n; v.w1 = base + 3 * n; v.w2 = base + 9 * n;
-    v.y1 = base + 15 * n; v.y2 = base + 17 * n; v.y3 = base + 19 * n; v.y4 = base + 20 * n;
+    v.u = base; v.s = base + P; v.t = base + 2 * P; v.w1 = base + 3 * P; v.w2 = base + 9 * P;
+    v.y1 = base + 15 * P; v.y2 = base + 17 * P; v.y3 = base + 19 * P; v.y4 = base + 20 * P;
     return v;
 }
 
@@ -580,7 +582,7 @@ struct Scratch {
 int gsstv_vjp_step(gsstv_handle* h, const gsstv_state_view* x, const gsstv_state_view* x_next,
                    const gsstv_state_view* bar_next, const gsstv_state_view* bar, float* d_vbar,
                    double* h_pbar) {
-    if (!h || !view_ok(x) || !view_ok(x_next) || !view_ok(bar_next) || !view_ok(bar) || !d_vbar || !h_pbar)
+    if (!h || !view_ok(x) || !view_ok(x_next) || !view_ok(bar_next) || !view_ok(bar) || !d_vbar)
         return GSSTV_ERR_ARG;
     if (h->p.storage != GSSTV_FP32) return GSSTV_ERR_ARG;
     const long long n = (long long)h->g.n1 * h->g.n2 * h->g.n3;
@@ -589,6 +591,7 @@ int gsstv_vjp_step(gsstv_handle* h, const gsstv_state_view* x, const gsstv_state
     double* d_pbar = (double*)((char*)h->adj_work + wb);
     TRY(cuda_rc(cudaMemsetAsync(d_pbar, 0, 4 * sizeof(double), h->st)));
     TRY(vjp_launch(h, x, x_next, bar_next, bar, d_vbar, d_pbar, h->adj_work));
+    if (!h_pbar) return GSSTV_OK;
     double pb[4];
     TRY(cuda_rc(cudaMemcpyAsync(pb, d_pbar, sizeof(pb), cudaMemcpyDeviceToHost, h->st)));
     TRY(cuda_rc(cudaStreamSynchronize(h->st)));
@@ -610,7 +613,8 @@ int gsstv_unrolled_vjp(gsstv_handle* h, int iters, int ckpt_every, const float* 
     const int C = ckpt_every > 0 ? std::min(ckpt_every, iters)
                                  : std::max(1, (int)std::ceil(std::sqrt((double)iters)));
     const int nck = (iters + C - 1) / C;
-    const size_t sbytes = kStateCubes * cube;
+    const long long P = adj_stride(n);
+    const size_t sbytes = (size_t)kStateCubes * P * sizeof(float);
     const size_t wb = adjoint_workspace_bytes(n);
     // nck checkpoints, C segment states, the adjoint state, the workspace
     Scratch scr;
@@ -620,9 +624,9 @@ int gsstv_unrolled_vjp(gsstv_handle* h, int iters, int ckpt_every, const float* 
         return GSSTV_ERR_OOM;
     }
     float* base = (float*)scr.p;
-    auto slot = [&](int k) { return state_at(base + (size_t)k * kStateCubes * n, n); };
+    auto slot = [&](int k) { return state_at(base + (size_t)k * kStateCubes * P, P); };
     const gsstv_state_view bar = slot(nck + C);
-    void* work = base + (size_t)(nck + C + 1) * kStateCubes * n;
+    void* work = base + (size_t)(nck + C + 1) * kStateCubes * P;
     double* d_pbar = (double*)((char*)work + wb);
     // forward: the state at the start of every segment (the last segment
     // needs no run here)

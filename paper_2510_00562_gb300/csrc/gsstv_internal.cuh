@@ -321,6 +321,9 @@ int launch_scale_unpack(int storage, const void* q, const double* c, float* dst,
 // vbar += the adjoint of v; pbar[0..3] += those of eps, alpha, beta, omega.
 // prm: g_u, g_w1, g_w2, g_s, g_t, g_y1..g_y4, thr_w1, thr_w2, mu_lo, mu_hi,
 // eps, alpha, beta.  work: adjoint_workspace_bytes(N) bytes.
+// Regions of the reverse mode's scratch start on 256-byte boundaries: a cube
+// of n floats takes adj_stride(n) floats (the global sums are doubles).
+inline long long adj_stride(long long n) { return (n + 63) / 64 * 64; }
 size_t adjoint_workspace_bytes(long long n);
 int launch_adjoint_step(int n1, int n2, int n3, const float* const x[9], const float* const x1[9],
                         const float* const b1[9], float* const bo[9], const float* v, int v_pitch,

@@ -123,17 +123,20 @@ class GeoSSTVSolver:
         B.gsstv_set_state(self.h, {k: v.data_ptr() for k, v in tens.items()})
 
     def vjp_step(self, x: dict, x_next: dict, bar_next: dict, vbar: torch.Tensor | None = None,
-                 in_place: bool = False):
+                 in_place: bool = False, want_params: bool = True):
         """Transpose of one pass (gsstv_vjp_step): x the state before it,
         x_next the state after it, bar_next the adjoint of x_next.  Returns
         (adjoint of x, adjoint of v, adjoints of eps/alpha/beta/omega); vbar,
-        if given, is accumulated into; in_place reuses bar_next's buffers."""
+        if given, is accumulated into; in_place reuses bar_next's buffers;
+        want_params=False skips the parameter adjoints (None) and the
+        synchronisation."""
         views = [{k: self._dev(d[k], STATE_LEAD[k]) for k in STATE_KEYS} for d in (x, x_next, bar_next)]
         bar = views[2] if in_place else {k: self._empty(STATE_LEAD[k]) for k in STATE_KEYS}
         vbar = torch.zeros(self.shape, dtype=torch.float32, device="cuda") if vbar is None else self._dev(vbar)
         ptr = lambda d: {k: t.data_ptr() for k, t in d.items()}
-        pb = B.gsstv_vjp_step(self.h, ptr(views[0]), ptr(views[1]), ptr(views[2]), ptr(bar), vbar.data_ptr())
-        return bar, vbar, dict(zip(GRAD_PARAMS, pb))
+        pb = B.gsstv_vjp_step(self.h, ptr(views[0]), ptr(views[1]), ptr(views[2]), ptr(bar), vbar.data_ptr(),
+                              want_params=want_params)
+        return bar, vbar, (dict(zip(GRAD_PARAMS, pb)) if want_params else None)
 
     def unrolled_vjp(self, iters: int, ubar: torch.Tensor, ckpt_every: int = 0):
         """Adjoint of `iters` passes from the standard start on the loaded

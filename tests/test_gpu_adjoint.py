@@ -124,9 +124,10 @@ def _denoise_problem(n1, n2, n3, seed):
     return pb
 
 
-@pytest.mark.parametrize("ckpt", [0, 1, 7, 40])
-def test_unrolled_gradient_matches_oracle(ckpt):
-    n1, n2, n3, iters = 24, 20, 6, 40
+@pytest.mark.parametrize("shape,ckpt", [((24, 20, 6), 0), ((24, 20, 6), 1), ((24, 20, 6), 7), ((24, 20, 6), 40),
+                                        ((23, 21, 5), 3)])       # odd voxel count
+def test_unrolled_gradient_matches_oracle(shape, ckpt):
+    (n1, n2, n3), iters = shape, 40
     pb = _denoise_problem(n1, n2, n3, seed=3)
     v = pb["v"].astype(np.float32)
     ub = pb["u_bar"].astype(np.float64)
