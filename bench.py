@@ -625,23 +625,29 @@ def run_grad(args):
         bwd_ms = ev_time(bwd, 3)
         free0, _ = torch.cuda.mem_get_info()
         scratch = ((K + C - 1) // C + C + 1) * 21 * N * 4 + 15 * N * 4 + 160
-        # central differences, step 1e-3 of each parameter
+        # central differences, steps 1e-3 and 1e-4 of each parameter
         fd = {}
         for k in GRAD_PARAMS:
-            h = 1e-3 * prm[k]
-            lp, _ = loss_of(v, **{k: prm[k] + h})
-            lm, _ = loss_of(v, **{k: prm[k] - h})
-            fd[k] = {"fd": (lp - lm) / (2 * h), "adjoint": pbar[k]}
-        # one direction in v, zero on the salt-and-pepper voxels (0 or 1
-        # exactly: the box's kinks, where only one-sided derivatives exist)
+            fd[k] = {"adjoint": pbar[k]}
+            for rs in (1e-3, 1e-4):
+                h = rs * prm[k]
+                lp, _ = loss_of(v, **{k: prm[k] + h})
+                lm, _ = loss_of(v, **{k: prm[k] - h})
+                fd[k][f"fd_{rs:g}"] = (lp - lm) / (2 * h)
+        # one direction in v, zero on the salt-and-pepper and dead voxels (0 or
+        # 1 exactly: the box's kinks, where only one-sided derivatives exist)
         g = torch.from_numpy(np.random.default_rng(1).standard_normal(pb["v"].shape).astype("float32")).cuda()
         g = torch.where((v == 0) | (v == 1), torch.zeros_like(g), g)
-        hv = 1e-3 * float(v.abs().mean())
-        lp, _ = loss_of((v + hv * g).contiguous())
-        lm, _ = loss_of((v - hv * g).contiguous())
-        fd["v_direction"] = {"fd": (lp - lm) / (2 * hv), "adjoint": float((vbar.double() * g.double()).sum())}
+        fd["v_direction"] = {"adjoint": float((vbar.double() * g.double()).sum())}
+        for rs in (1e-3, 1e-4):
+            hv = rs * float(v.abs().mean())
+            lp, _ = loss_of((v + hv * g).contiguous())
+            lm, _ = loss_of((v - hv * g).contiguous())
+            fd["v_direction"][f"fd_{rs:g}"] = (lp - lm) / (2 * hv)
         for ent in fd.values():
-            ent["rel_diff"] = abs(ent["fd"] - ent["adjoint"]) / max(abs(ent["fd"]), 1e-300)
+            for rs in ("0.001", "0.0001"):
+                f_ = ent[f"fd_{rs}"]
+                ent[f"rel_diff_{rs}"] = abs(f_ - ent["adjoint"]) / max(abs(f_), 1e-300)
         sol.set_params(**prm)
         # the transposed pass alone, in place, no parameter read-back
         sol.load(v)

@@ -43,6 +43,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "gsstv_internal.cuh"
 
@@ -55,10 +56,8 @@ struct Dims {
     int n1, n2, n3;
     int vp;                                       // row pitch of v (floats)
     int rows;                                     // n3 * n1
+    long long plane;                              // n1 * n2
     long long N;                                  // voxels
-    __device__ __forceinline__ long long at(int b, int i, int j) const {
-        return ((long long)b * n1 + i) * n2 + j;
-    }
 };
 
 struct SV {
@@ -88,56 +87,75 @@ struct AdjArgs {
 // read-only data (states k, k+1 and v; never written during a pass)
 __device__ __forceinline__ float rd(const float* p, long long k) { return __ldg(p + k); }
 
-// ---- stencils on dense cubes (value at (b, i, j) of an operator's output) ----
-// They read through the read-only path: every kernel applies them only to
-// arrays that no thread writes while it runs.
-__device__ __forceinline__ float ld(const float* p, const Dims& d, int b, int i, int j) {
-    return (i >= 0 && i < d.n1 && j >= 0 && j < d.n2 && b >= 0 && b < d.n3) ? rd(p, d.at(b, i, j)) : 0.f;
+// ---- stencils on dense cubes (value at voxel l = (b, i, j) of an operator's
+// output).  They read through the read-only path: every kernel applies them
+// only to arrays that no thread writes while it runs.  IN = the voxel is
+// interior in its band (1 <= i <= N1-2, 1 <= j <= N2-2): then every spatial
+// neighbour they touch exists and no boundary mask applies, so the checks
+// are compiled out; the band neighbours are checked either way.
+
+// p at (b, i+di, j+dj), zero outside the image
+template <bool IN>
+__device__ __forceinline__ float nb(const float* p, const Dims& d, long long l, int i, int j, int di, int dj) {
+    if (!IN && (i + di < 0 || i + di >= d.n1 || j + dj < 0 || j + dj >= d.n2)) return 0.f;
+    return rd(p, l + (long long)di * d.n2 + dj);
 }
-__device__ __forceinline__ float dv(const float* x, const Dims& d, int b, int i, int j) {
-    return i < d.n1 - 1 ? rd(x, d.at(b, i + 1, j)) - rd(x, d.at(b, i, j)) : 0.f;
+// D_v x, D_h x
+template <bool IN>
+__device__ __forceinline__ float dv(const float* x, const Dims& d, long long l, int i) {
+    return (IN || i < d.n1 - 1) ? rd(x, l + d.n2) - rd(x, l) : 0.f;
 }
-__device__ __forceinline__ float dh(const float* x, const Dims& d, int b, int i, int j) {
-    return j < d.n2 - 1 ? rd(x, d.at(b, i, j + 1)) - rd(x, d.at(b, i, j)) : 0.f;
+template <bool IN>
+__device__ __forceinline__ float dh(const float* x, const Dims& d, long long l, int j) {
+    return (IN || j < d.n2 - 1) ? rd(x, l + 1) - rd(x, l) : 0.f;
 }
 // transposes: (D_v^T y)(i) = y(i-1) [i >= 1] - y(i) [i <= N1-2]
-__device__ __forceinline__ float dvT(const float* y, const Dims& d, int b, int i, int j) {
+template <bool IN>
+__device__ __forceinline__ float dvT(const float* y, const Dims& d, long long l, int i) {
     float r = 0.f;
-    if (i >= 1) r += rd(y, d.at(b, i - 1, j));
-    if (i <= d.n1 - 2) r -= rd(y, d.at(b, i, j));
+    if (IN || i >= 1) r += rd(y, l - d.n2);
+    if (IN || i <= d.n1 - 2) r -= rd(y, l);
     return r;
 }
-__device__ __forceinline__ float dhT(const float* y, const Dims& d, int b, int i, int j) {
+template <bool IN>
+__device__ __forceinline__ float dhT(const float* y, const Dims& d, long long l, int j) {
     float r = 0.f;
-    if (j >= 1) r += rd(y, d.at(b, i, j - 1));
-    if (j <= d.n2 - 2) r -= rd(y, d.at(b, i, j));
+    if (IN || j >= 1) r += rd(y, l - 1);
+    if (IN || j <= d.n2 - 2) r -= rd(y, l);
     return r;
 }
 // D^T y for a dual pair y (2 planes of N)
-__device__ __forceinline__ float dT(const float* y, const Dims& d, int b, int i, int j) {
-    return dvT(y, d, b, i, j) + dhT(y + d.N, d, b, i, j);
+template <bool IN>
+__device__ __forceinline__ float dT(const float* y, const Dims& d, long long l, int i, int j) {
+    return dvT<IN>(y, d, l, i) + dhT<IN>(y + d.N, d, l, j);
 }
 // (D_s^T D^T y)(b) = (D^T y)(b-1) [b >= 1] - (D^T y)(b) [b <= N3-2]
-__device__ __forceinline__ float dsT_dT(const float* y, const Dims& d, int b, int i, int j) {
+template <bool IN>
+__device__ __forceinline__ float dsT_dT(const float* y, const Dims& d, long long l, int b, int i, int j) {
     float r = 0.f;
-    if (b >= 1) r += dT(y, d, b - 1, i, j);
-    if (b <= d.n3 - 2) r -= dT(y, d, b, i, j);
+    if (b >= 1) r += dT<IN>(y, d, l - d.plane, i, j);
+    if (b <= d.n3 - 2) r -= dT<IN>(y, d, l, i, j);
     return r;
 }
-// masked dual-pair entries read by L
-__device__ __forceinline__ float yvm(const float* y, const Dims& d, int b, int i, int j) {
-    return (i >= 0 && i < d.n1 - 1 && j >= 0 && j < d.n2) ? rd(y, d.at(b, i, j)) : 0.f;
+// dual-pair entries read by L, masked where D is structurally zero
+template <bool IN>
+__device__ __forceinline__ float yvm(const float* y, const Dims& d, long long l, int i, int j, int di, int dj) {
+    if (!IN && !(i + di >= 0 && i + di < d.n1 - 1 && j + dj >= 0 && j + dj < d.n2)) return 0.f;
+    return rd(y, l + (long long)di * d.n2 + dj);
 }
-__device__ __forceinline__ float yhm(const float* y, const Dims& d, int b, int i, int j) {
-    return (i >= 0 && i < d.n1 && j >= 0 && j < d.n2 - 1) ? rd(y, d.N + d.at(b, i, j)) : 0.f;
+template <bool IN>
+__device__ __forceinline__ float yhm(const float* y, const Dims& d, long long l, int i, int j, int di, int dj) {
+    if (!IN && !(i + di >= 0 && i + di < d.n1 && j + dj >= 0 && j + dj < d.n2 - 1)) return 0.f;
+    return rd(y, d.N + l + (long long)di * d.n2 + dj);
 }
-// L y at (b, i, j): out[k], k = 2 g + c (g grid, c = vertical / horizontal)
-__device__ __forceinline__ void Lop(const float* y, const Dims& d, int b, int i, int j, float out[6]) {
-    const float v00 = yvm(y, d, b, i, j), vm0 = yvm(y, d, b, i - 1, j), v01 = yvm(y, d, b, i, j + 1),
-                vm1 = yvm(y, d, b, i - 1, j + 1);
-    const float h00 = yhm(y, d, b, i, j), h0m = yhm(y, d, b, i, j - 1), h10 = yhm(y, d, b, i + 1, j),
-                h1m = yhm(y, d, b, i + 1, j - 1);
-    const bool mv = i < d.n1 - 1, mh = j < d.n2 - 1;
+// L y: out[k], k = 2 g + c (g grid, c = vertical / horizontal)
+template <bool IN>
+__device__ __forceinline__ void Lop(const float* y, const Dims& d, long long l, int i, int j, float out[6]) {
+    const float v00 = yvm<IN>(y, d, l, i, j, 0, 0), vm0 = yvm<IN>(y, d, l, i, j, -1, 0),
+                v01 = yvm<IN>(y, d, l, i, j, 0, 1), vm1 = yvm<IN>(y, d, l, i, j, -1, 1);
+    const float h00 = yhm<IN>(y, d, l, i, j, 0, 0), h0m = yhm<IN>(y, d, l, i, j, 0, -1),
+                h10 = yhm<IN>(y, d, l, i, j, 1, 0), h1m = yhm<IN>(y, d, l, i, j, 1, -1);
+    const bool mv = IN || i < d.n1 - 1, mh = IN || j < d.n2 - 1;
     out[0] = mv ? v00 : 0.f;
     out[1] = mv ? 0.25f * (h00 + h0m + h10 + h1m) : 0.f;
     out[2] = mh ? 0.25f * (v00 + vm0 + v01 + vm1) : 0.f;
@@ -145,25 +163,31 @@ __device__ __forceinline__ void Lop(const float* y, const Dims& d, int b, int i,
     out[4] = 0.5f * (v00 + vm0);
     out[5] = 0.5f * (h00 + h0m);
 }
-// component k of w at (b, i, j), zero outside the image and where L's
+// component k of w at (b, i+di, j+dj), zero outside the image and where L's
 // output is structurally zero (grid 0 on the last row, grid 1 on the last column)
-__device__ __forceinline__ float wk(const float* w, const Dims& d, int k, int b, int i, int j) {
-    if (i < 0 || i >= d.n1 || j < 0 || j >= d.n2) return 0.f;
-    if (k < 2 && i == d.n1 - 1) return 0.f;
-    if ((k == 2 || k == 3) && j == d.n2 - 1) return 0.f;
-    return rd(w, (long long)k * d.N + d.at(b, i, j));
+template <bool IN>
+__device__ __forceinline__ float wk(const float* w, const Dims& d, int k, long long l, int i, int j, int di, int dj) {
+    if (!IN) {
+        const int ii = i + di, jj = j + dj;
+        if (ii < 0 || ii >= d.n1 || jj < 0 || jj >= d.n2) return 0.f;
+        if (k < 2 && ii == d.n1 - 1) return 0.f;
+        if ((k == 2 || k == 3) && jj == d.n2 - 1) return 0.f;
+    }
+    return rd(w, (long long)k * d.N + l + (long long)di * d.n2 + dj);
 }
-// L^T w at (b, i, j): (vertical, horizontal)
-__device__ __forceinline__ void LTop(const float* w, const Dims& d, int b, int i, int j, float& gv, float& gh) {
-    const bool mv = i < d.n1 - 1, mh = j < d.n2 - 1;
-    gv = mv ? (wk(w, d, 0, b, i, j) +
-               0.25f * (wk(w, d, 2, b, i, j) + wk(w, d, 2, b, i + 1, j) + wk(w, d, 2, b, i, j - 1) +
-                        wk(w, d, 2, b, i + 1, j - 1)) +
-               0.5f * (wk(w, d, 4, b, i, j) + wk(w, d, 4, b, i + 1, j)))
+// L^T w: (vertical, horizontal)
+template <bool IN>
+__device__ __forceinline__ void LTop(const float* w, const Dims& d, long long l, int i, int j, float& gv, float& gh) {
+    const bool mv = IN || i < d.n1 - 1, mh = IN || j < d.n2 - 1;
+    gv = mv ? (wk<IN>(w, d, 0, l, i, j, 0, 0) +
+               0.25f * (wk<IN>(w, d, 2, l, i, j, 0, 0) + wk<IN>(w, d, 2, l, i, j, 1, 0) +
+                        wk<IN>(w, d, 2, l, i, j, 0, -1) + wk<IN>(w, d, 2, l, i, j, 1, -1)) +
+               0.5f * (wk<IN>(w, d, 4, l, i, j, 0, 0) + wk<IN>(w, d, 4, l, i, j, 1, 0)))
             : 0.f;
-    gh = mh ? (0.25f * (wk(w, d, 1, b, i, j) + wk(w, d, 1, b, i, j + 1) + wk(w, d, 1, b, i - 1, j) +
-                        wk(w, d, 1, b, i - 1, j + 1)) +
-               wk(w, d, 3, b, i, j) + 0.5f * (wk(w, d, 5, b, i, j) + wk(w, d, 5, b, i, j + 1)))
+    gh = mh ? (0.25f * (wk<IN>(w, d, 1, l, i, j, 0, 0) + wk<IN>(w, d, 1, l, i, j, 0, 1) +
+                        wk<IN>(w, d, 1, l, i, j, -1, 0) + wk<IN>(w, d, 1, l, i, j, -1, 1)) +
+               wk<IN>(w, d, 3, l, i, j, 0, 0) +
+               0.5f * (wk<IN>(w, d, 5, l, i, j, 0, 0) + wk<IN>(w, d, 5, l, i, j, 0, 1)))
             : 0.f;
 }
 
@@ -180,15 +204,24 @@ __device__ __forceinline__ double block_sum_d(double x, double* buf) {
 }
 
 // The voxels of this thread: column j of the block, rows (b*N1 + i) strided
-// by the grid; body(b, i, j, l) per voxel.
+// by the grid; body(b, i, j, l, interior) per voxel, interior a
+// std::integral_constant<bool, ...> selecting the unchecked stencils.  The
+// choice is made per warp (one row, 32 columns): a warp with a border voxel
+// takes the checked path for all its lanes, so no warp runs both.
 template <int UNROLL = 1, class F>
 __device__ __forceinline__ void for_voxels(const Dims& d, F&& body) {
     const int j = blockIdx.x * BX + threadIdx.x;
     if (j >= d.n2) return;
+    const unsigned lanes = __activemask();          // the same lanes in every iteration
+    const bool jin = j >= 1 && j <= d.n2 - 2;
 #pragma unroll UNROLL
     for (int row = blockIdx.y * BY + threadIdx.y; row < d.rows; row += gridDim.y * BY) {
         const int b = row / d.n1, i = row - b * d.n1;
-        body(b, i, j, (long long)row * d.n2 + j);
+        const long long l = (long long)row * d.n2 + j;
+        if (__all_sync(lanes, jin && i >= 1 && i <= d.n1 - 2))
+            body(b, i, j, l, std::true_type{});
+        else
+            body(b, i, j, l, std::false_type{});
     }
 }
 
@@ -226,13 +259,15 @@ __device__ __forceinline__ float q_at(const AdjArgs& a, long long l, int b, int 
 __global__ void __launch_bounds__(NTA, 4) k_adj_sums(const AdjArgs a) {
     __shared__ double buf[BY];
     Partial<4> p;
-    for_voxels<2>(a.d, [&](int b, int i, int j, long long l) {
+    for_voxels<2>(a.d, [&](int b, int i, int j, long long l, auto in) {
+        constexpr bool IN = decltype(in)::value;
+        (void)b;
         const float q = q_at(a, l, b, i, j);
         const float y4 = rd(a.x.y4, l);
         p.f[0] = fmaf(q, q, p.f[0]);
         p.f[1] = fmaf(q, rd(a.b1.y4, l), p.f[1]);
         p.f[2] += fabsf(rd(a.x.s, l) - a.g_s * y4);
-        p.f[3] += fabsf(rd(a.x.t, l) - a.g_t * (dvT(a.x.y3, a.d, b, i, j) + y4));
+        p.f[3] += fabsf(rd(a.x.t, l) - a.g_t * (dvT<IN>(a.x.y3, a.d, l, i) + y4));
         p.step();
     });
     p.flush();
@@ -268,14 +303,15 @@ __global__ void __launch_bounds__(NTA, 4) k_adj_cube(const AdjArgs a) {
     const float fk = scal[1], qs = scal[2];
     Partial<2> p;
     unsigned ns = 0, nt = 0;
-    for_voxels(d, [&](int b, int i, int j, long long l) {
+    for_voxels(d, [&](int b, int i, int j, long long l, auto in) {
+        constexpr bool IN = decltype(in)::value;
         // loads of the buffers that this kernel also writes (in place), first
         const float y4b = a.b1.y4[l], bu = a.b1.u[l], bs = a.b1.s[l], bt = a.b1.t[l], vb = a.vbar[l];
         // y4+ = (1 - c) q
         const float qbar = l2act ? y4b - fk * (y4b - q_at(a, l, b, i, j) * qs) : 0.f;
-        const float ub_ = a.g4 * qbar + a.g2 * dsT_dT(a.b1.y2, d, b, i, j) + a.g1 * dT(a.b1.y1, d, b, i, j);
+        const float ub_ = a.g4 * qbar + a.g2 * dsT_dT<IN>(a.b1.y2, d, l, b, i, j) + a.g1 * dT<IN>(a.b1.y1, d, l, i, j);
         const float sb_ = a.g4 * qbar;
-        const float tb_ = a.g4 * qbar + a.g3 * dvT(a.b1.y3, d, b, i, j);
+        const float tb_ = a.g4 * qbar + a.g3 * dvT<IN>(a.b1.y3, d, l, i);
         // u+ = box(a_u): the adjoint passes where mu_lo < u+ < mu_hi
         const float u1 = rd(a.x1.u, l);
         const float u1bar = bu + 2.f * ub_;
@@ -322,7 +358,8 @@ __global__ void __launch_bounds__(NTA, 4) k_adj_aux(const AdjArgs a) {
     const Dims& d = a.d;
     const long long N = d.N;
     Partial<1> p;
-    for_voxels(d, [&](int b, int i, int j, long long l) {
+    for_voxels(d, [&](int b, int i, int j, long long l, auto in) {
+        constexpr bool IN = decltype(in)::value;
         // the adjoints of w1+, w2+ (this kernel overwrites them in place), first
         float pw[12];
 #pragma unroll
@@ -339,8 +376,8 @@ __global__ void __launch_bounds__(NTA, 4) k_adj_aux(const AdjArgs a) {
             const float gy = set ? a.g2 : a.g1;
             const float thr = set ? a.th2 : a.th1;
             float lw[6], ly[6];
-            Lop(set ? a.b1.y2 : a.b1.y1, d, b, i, j, lw);
-            Lop(set ? a.x.y2 : a.x.y1, d, b, i, j, ly);
+            Lop<IN>(set ? a.b1.y2 : a.b1.y1, d, l, i, j, lw);
+            Lop<IN>(set ? a.x.y2 : a.x.y1, d, l, i, j, ly);
 #pragma unroll
             for (int g = 0; g < 3; ++g) {
                 const long long kv = (long long)(2 * g) * N + l, kh = (long long)(2 * g + 1) * N + l;
@@ -351,9 +388,10 @@ __global__ void __launch_bounds__(NTA, 4) k_adj_aux(const AdjArgs a) {
                 const float n = sqrtf(xv * xv + xh * xh);
                 float av = 0.f, ah = 0.f;
                 if (n > thr) {
-                    const float xhv = xv / n, xhh = xh / n;
+                    const float rn = 1.f / n;
+                    const float xhv = xv * rn, xhh = xh * rn;
                     const float dot = xhv * pv + xhh * ph;
-                    const float k1 = 1.f - thr / n, k2 = thr / n;
+                    const float k2 = thr * rn, k1 = 1.f - k2;
                     av = k1 * pv + k2 * xhv * dot;
                     ah = k1 * ph + k2 * xhh * dot;
                     if (set == 0) p.f[0] -= dot;
@@ -399,7 +437,8 @@ __global__ void __launch_bounds__(NTA, 4) k_adj_fin1(const AdjArgs a) {
         const float t1 = rd(a.x1.t, l), tb = rd(a.t1b, l);
         return in_t ? tb : (t1 != 0.f ? tb - (t1 > 0.f ? kt : -kt) : 0.f);
     };
-    for_voxels(d, [&](int b, int i, int j, long long l) {
+    for_voxels(d, [&](int b, int i, int j, long long l, auto in) {
+        (void)b; (void)j; (void)in;                 // pointwise (no stencils)
         // the adjoint entries updated here, first
         const float bs = a.b.s[l], bt = a.b.t[l], b4 = a.b.y4[l], b3 = a.b.y3[l];
         const float s1 = rd(a.x1.s, l), s1b = rd(a.s1b, l);
@@ -419,18 +458,20 @@ __global__ void __launch_bounds__(NTA, 4) k_adj_fin1(const AdjArgs a) {
 __global__ void __launch_bounds__(NTA, 4) k_adj_fin2(const AdjArgs a) {
     const Dims& d = a.d;
     const long long N = d.N;
-    for_voxels(d, [&](int b, int i, int j, long long l) {
+    for_voxels(d, [&](int b, int i, int j, long long l, auto in) {
+        constexpr bool IN = decltype(in)::value;
         // the adjoint entries updated here, first
         const float b1v = a.b.y1[l], b1h = a.b.y1[N + l], b2v = a.b.y2[l], b2h = a.b.y2[N + l];
         float gv1, gh1, gv2, gh2;
-        LTop(a.aw1, d, b, i, j, gv1, gh1);
-        LTop(a.aw2, d, b, i, j, gv2, gh2);
-        auto dsg = [&](int ii, int jj) {           // (D_s G_bar)(b, ii, jj)
-            return b < d.n3 - 1 ? ld(a.gbar, d, b + 1, ii, jj) - ld(a.gbar, d, b, ii, jj) : 0.f;
+        LTop<IN>(a.aw1, d, l, i, j, gv1, gh1);
+        LTop<IN>(a.aw2, d, l, i, j, gv2, gh2);
+        const bool up = b < d.n3 - 1;
+        auto dsg = [&](int di, int dj) {           // (D_s G_bar)(b, i+di, j+dj)
+            return up ? nb<IN>(a.gbar, d, l + d.plane, i, j, di, dj) - nb<IN>(a.gbar, d, l, i, j, di, dj) : 0.f;
         };
-        const float dvg = dv(a.gbar, d, b, i, j), dhg = dh(a.gbar, d, b, i, j);
-        const float dvds = i < d.n1 - 1 ? dsg(i + 1, j) - dsg(i, j) : 0.f;
-        const float dhds = j < d.n2 - 1 ? dsg(i, j + 1) - dsg(i, j) : 0.f;
+        const float dvg = dv<IN>(a.gbar, d, l, i), dhg = dh<IN>(a.gbar, d, l, j);
+        const float dvds = (IN || i < d.n1 - 1) ? dsg(1, 0) - dsg(0, 0) : 0.f;
+        const float dhds = (IN || j < d.n2 - 1) ? dsg(0, 1) - dsg(0, 0) : 0.f;
         a.b.y1[l] = b1v + (dvg + a.g_w1 * gv1);
         a.b.y1[N + l] = b1h + (dhg + a.g_w1 * gh1);
         a.b.y2[l] = b2v + (dvds + a.g_w2 * gv2);
@@ -494,6 +535,7 @@ int launch_adjoint_step(int n1, int n2, int n3, const float* const x[9], const f
     AdjArgs a;
     a.d.n1 = n1; a.d.n2 = n2; a.d.n3 = n3; a.d.vp = v_pitch;
     a.d.rows = n3 * n1;
+    a.d.plane = (long long)n1 * n2;
     a.d.N = (long long)n1 * n2 * n3;
     const long long N = a.d.N;
     a.x = SV{x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], x[8]};

@@ -10,7 +10,10 @@ Tolerances (relative L2 error per variable):
   * K passes from the standard start: 1e-3 on v_bar and on each parameter
     adjoint -- the float32 forward trajectory drifts from the FP64 one by
     ~1e-6 relative per pass and the adjoint sweep adds its own rounding at
-    every pass.
+    every pass;
+  * against central differences of the float32 forward run (step 1e-3 of
+    each parameter): 1e-2 -- the secant over that step crosses kinks of the
+    box, the shrinkage and the l1 projections, where the derivative jumps.
 """
 import math
 
@@ -165,6 +168,28 @@ def test_unrolled_gradient_does_not_depend_on_the_checkpoint_spacing():
         assert rel(vb.cpu().numpy(), out[0][0].cpu().numpy()) < 1e-4
         for k in GRAD_PARAMS:
             assert pbar[k] == pytest.approx(out[0][1][k], rel=1e-4, abs=1e-12), k
+
+
+def test_unrolled_gradient_vs_central_differences():
+    """The GPU gradient against central differences of the GPU forward run."""
+    n1, n2, n3, iters = 48, 40, 16, 60
+    pb = _denoise_problem(n1, n2, n3, seed=6)
+    v = to_dev(pb["v"])
+    ub = torch.from_numpy(pb["u_bar"].astype(np.float64)).cuda()
+    prm = dict(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.05)
+    with GeoSSTVSolver(n1, n2, n3, make_params(graph_iters=16, max_iter=iters, **prm)) as sol:
+        def loss(**over):
+            sol.set_params(**{**prm, **over})
+            u, _, _, _ = sol.solve(v)
+            return float(((u.double() - ub) ** 2).mean()), u
+
+        l0, u = loss()
+        sol.load(v)
+        _, pbar = sol.unrolled_vjp(iters, ((2.0 / v.numel()) * (u.double() - ub)).float().contiguous())
+        for k in GRAD_PARAMS:
+            h = 1e-3 * prm[k]
+            fd = (loss(**{k: prm[k] + h})[0] - loss(**{k: prm[k] - h})[0]) / (2 * h)
+            assert pbar[k] == pytest.approx(fd, rel=1e-2), (k, pbar[k], fd)
 
 
 def test_zero_iterations_is_the_identity():
