@@ -624,7 +624,20 @@ def run_grad(args):
         vbar, pbar = bwd()
         bwd_ms = ev_time(bwd, 3)
         free0, _ = torch.cuda.mem_get_info()
-        scratch = ((K + C - 1) // C + C + 1) * 21 * N * 4 + 15 * N * 4 + 160
+        P = (N + 63) // 64 * 64
+        scratch = ((K + C - 1) // C + C + 1) * 21 * P * 4 + 15 * P * 4 + 160
+        # every state kept (checkpoint every pass): nothing run twice
+        keep_bytes = (K + 2) * 21 * P * 4 + 15 * P * 4 + 160
+        keep = None
+        if keep_bytes < 0.8 * free0:
+            def bwd_keep():
+                sol.load(v)
+                return sol.unrolled_vjp(K, seed, ckpt_every=1)
+            vk, pk = bwd_keep()
+            keep = {"backward_ms": ev_time(bwd_keep, 3), "scratch_bytes": keep_bytes,
+                    "max_rel_diff_params": max(abs(pk[k] - pbar[k]) / abs(pbar[k]) for k in GRAD_PARAMS),
+                    "rel_diff_vbar": float((vk - vbar).norm() / vbar.norm())}
+            keep["backward_over_forward"] = keep["backward_ms"] / fwd_ms
         # central differences, steps 1e-3 and 1e-4 of each parameter
         fd = {}
         for k in GRAD_PARAMS:
@@ -667,6 +680,7 @@ def run_grad(args):
         "loss": "mean((u_K - u_bar)^2)", "loss_value": loss,
         "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
         "checkpoint_every": C, "scratch_bytes": scratch, "handle_bytes": handle_bytes,
+        "every_state_kept": keep,
         "free_bytes_after_backward": free0,
         "gradients_vs_central_differences": fd,
         "adjoint_pass": {"ms": step_ms, "kernels": 5, "algorithmic_bytes_per_voxel": ADJ_WORDS * 4,

@@ -225,7 +225,8 @@ int gsstv_batch_destroy(gsstv_batch* b);
  * C = min(ckpt_every, iters) the call allocates ceil(iters/C) + C + 1 states
  * of 21 N floats and a 16 N-float workspace with cudaMalloc and frees them
  * before returning (GSSTV_ERR_OOM if they do not fit), runs the passes about
- * twice in all, and leaves the handle's state unspecified (reset it before
+ * twice in all (once with ckpt_every = 1: every state is kept and nothing is
+ * run again), and leaves the handle's state unspecified (reset it before
  * iterating again).  Synchronises the stream. */
 int gsstv_vjp_step(gsstv_handle* h, const gsstv_state_view* x, const gsstv_state_view* x_next,
                    const gsstv_state_view* bar_next, const gsstv_state_view* bar, float* d_vbar,

@@ -628,13 +628,20 @@ int gsstv_unrolled_vjp(gsstv_handle* h, int iters, int ckpt_every, const float* 
     const gsstv_state_view bar = slot(nck + C);
     void* work = base + (size_t)(nck + C + 1) * kStateCubes * P;
     double* d_pbar = (double*)((char*)work + wb);
-    // forward: the state at the start of every segment (the last segment
-    // needs no run here)
+    // forward: the state at the start of every segment.  With a checkpoint
+    // every pass (C = 1) the forward keeps every state, the last one in the
+    // (otherwise unused) first segment slot, and the sweep re-runs nothing;
+    // otherwise the last segment needs no run here.
+    const bool keep_all = C == 1;
     TRY(gsstv_reset_state(h));
     for (int c = 0; c < nck; ++c) {
         const gsstv_state_view v = slot(c);
         TRY(enqueue_get_state(h, &v));
-        if (c + 1 < nck) TRY(run_block(h, C));
+        if (c + 1 < nck || keep_all) TRY(run_block(h, C));
+    }
+    if (keep_all) {
+        const gsstv_state_view v = slot(nck);
+        TRY(enqueue_get_state(h, &v));
     }
     TRY(flush_timing(h));
     Scal sc;
@@ -645,7 +652,13 @@ int gsstv_unrolled_vjp(gsstv_handle* h, int iters, int ckpt_every, const float* 
     TRY(cuda_rc(cudaMemcpyAsync(bar.u, d_ubar, cube, cudaMemcpyDeviceToDevice, h->st)));
     TRY(cuda_rc(cudaMemsetAsync(d_vbar, 0, cube, h->st)));
     TRY(cuda_rc(cudaMemsetAsync(d_pbar, 0, 4 * sizeof(double), h->st)));
-    for (int c = nck - 1; c >= 0; --c) {
+    if (keep_all) {
+        for (int k = iters - 1; k >= 0; --k) {
+            const gsstv_state_view xk = slot(k), xk1 = slot(k + 1);
+            TRY(vjp_launch(h, &xk, &xk1, &bar, &bar, d_vbar, d_pbar, work));
+        }
+    }
+    for (int c = keep_all ? -1 : nck - 1; c >= 0; --c) {
         const int len = std::min(C, iters - c * C);
         const gsstv_state_view start = slot(c);
         TRY(gsstv_set_state(h, &start));

@@ -521,20 +521,23 @@ __global__ void k_apply_flat(const float* x, float* out, long long n, const Scal
 // ---------------------------------------------------------------------------
 // layout conversion: (ncubes, n3, n1, *) arrays between pitches and types
 // ---------------------------------------------------------------------------
+// Row by row: blocks in y walk the rows of all cubes (one division per row),
+// threads in x the columns.
 template <typename S, typename D>
 __global__ void k_convert(const S* src, long long src_pitch, long long src_cube, D* dst,
                           long long dst_pitch, long long dst_cube, int n1, int n2, int n3,
                           int ncubes, const double* scale) {
     const float f = scale ? (float)(1.0 - *scale) : 1.f;
-    const long long per = (long long)n3 * n1 * n2;
-    const long long total = per * ncubes;
-    for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < total; l += (long long)gridDim.x * NT) {
-        const int cb = (int)(l / per);
-        const long long r = l - cb * per;
-        const long long row = r / n2;             // b * n1 + i
-        const int j = (int)(r - row * n2);
-        const float x = ldT(src + cb * src_cube + row * src_pitch + j);
-        stT(dst + cb * dst_cube + row * dst_pitch + j, scale ? f * x : x);
+    const long long rows = (long long)n3 * n1;
+    const long long total = rows * ncubes;
+    for (long long r = blockIdx.y; r < total; r += gridDim.y) {
+        const long long cb = r / rows, row = r - cb * rows;    // row = b * n1 + i
+        const S* s = src + cb * src_cube + row * src_pitch;
+        D* d = dst + cb * dst_cube + row * dst_pitch;
+        for (int j = blockIdx.x * NT + threadIdx.x; j < n2; j += gridDim.x * NT) {
+            const float x = ldT(s + j);
+            stT(d + j, scale ? f * x : x);
+        }
     }
 }
 
@@ -613,8 +616,11 @@ int launch_window_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal*
 template <typename S, typename D>
 int launch_convert(const S* src, long long sp, long long sc_, D* dst, long long dp, long long dc,
                    const Geom& g, int ncubes, const double* scale, cudaStream_t st) {
-    const long long n = (long long)g.n3 * g.n1 * g.n2 * ncubes;
-    k_convert<S, D><<<grid_for(n), NT, 0, st>>>(src, sp, sc_, dst, dp, dc, g.n1, g.n2, g.n3, ncubes, scale);
+    const long long rows = (long long)g.n3 * g.n1 * ncubes;
+    const int gx = (g.n2 + NT - 1) / NT;
+    const long long gy = std::max(1ll, std::min({rows, (152ll * 16) / gx, 65535ll}));
+    k_convert<S, D><<<dim3(gx, (unsigned)gy), NT, 0, st>>>(src, sp, sc_, dst, dp, dc, g.n1, g.n2, g.n3,
+                                                           ncubes, scale);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
