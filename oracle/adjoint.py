@@ -160,24 +160,39 @@ def unrolled(v, p: o.Params, iters: int, state: o.State | None = None):
     return traj
 
 
-def unrolled_grad(v, u_ref, p: o.Params, iters: int):
+def unrolled_grad(v, u_ref, p: o.Params, iters: int, ckpt_every: int | None = None):
     """Loss = mean((u_K - u_ref)^2) after ``iters`` passes from the standard
-    start (u = v, the rest zero).  Returns (loss, v_bar, params_bar)."""
+    start (u = v, the rest zero).  Returns (loss, v_bar, params_bar).
+
+    ckpt_every: keep only every ckpt_every-th state and run each segment
+    again from it during the reverse sweep (the same arithmetic, less
+    memory); None keeps the whole trajectory."""
     v = np.asarray(v, dtype=np.float64)
-    traj = unrolled(v, p, iters)
-    uk = traj[-1].u
+    C = iters if not ckpt_every else max(1, min(int(ckpt_every), iters))
+    # forward: the states at passes 0, C, 2C, ... and the last one
+    ckpt = {}
+    st = o.init_state(v)
+    for k in range(iters):
+        if k % C == 0:
+            ckpt[k] = st
+        st = o.ppds_step(st, v, p)
+    last = st
+    uk = last.u
     n = uk.size
     loss = float(np.mean((uk - u_ref) ** 2))
     z = lambda x: np.zeros_like(x)
-    last = traj[-1]
     bar = o.State(u=2.0 * (uk - u_ref) / n, s=z(last.s), t=z(last.t), w1=z(last.w1), w2=z(last.w2),
                   y1=z(last.y1), y2=z(last.y2), y3=z(last.y3), y4=z(last.y4))
     vbar = np.zeros_like(v)
     pbar = {k: 0.0 for k in PARAMS}
-    for k in range(iters - 1, -1, -1):
-        bar, vb, pb = step_vjp(traj[k], v, p, bar)
-        vbar += vb
-        for key in PARAMS:
-            pbar[key] += pb[key]
+    for start in sorted(ckpt, reverse=True):
+        seg = [ckpt[start]]                # the segment's states, run again from its checkpoint
+        for _ in range(start + 1, min(start + C, iters)):
+            seg.append(o.ppds_step(seg[-1], v, p))
+        for st_k in reversed(seg):
+            bar, vb, pb = step_vjp(st_k, v, p, bar)
+            vbar += vb
+            for key in PARAMS:
+                pbar[key] += pb[key]
     vbar += bar.u                          # the start u = v
     return loss, vbar, pbar

@@ -120,3 +120,19 @@ def test_unrolled_grad_matches_central_differences():
         hk = 1e-6 * x
         fk = (L(v, _with(p, **{k: x + hk})) - L(v, _with(p, **{k: x - hk}))) / (2 * hk)
         assert pbar[k] == pytest.approx(fk, rel=1e-4, abs=1e-12), k
+
+
+def test_unrolled_grad_checkpointing_changes_nothing():
+    """Running segments again from checkpoints repeats the same FP64
+    arithmetic: the gradient is bit-identical to the one from the kept
+    trajectory."""
+    pb = synth.make_problem(6, 5, 4, seed=4)
+    v = pb["v"].astype(np.float64)
+    ub = pb["u_bar"].astype(np.float64)
+    p = o.Params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.05)
+    ref = A.unrolled_grad(v, ub, p, 11)
+    for c in (1, 3, 4, 11, 50):
+        got = A.unrolled_grad(v, ub, p, 11, ckpt_every=c)
+        assert got[0] == ref[0]
+        assert np.array_equal(got[1], ref[1])
+        assert got[2] == ref[2]
