@@ -567,6 +567,60 @@ def run_precision_study(args):
     return 0
 
 
+QUALITY_SHAPES = ((256, 256, 128), (512, 512, 224))
+QUALITY_SIGMAS = (0.05, 0.1)
+QUALITY_SP = (0.05, 0.1)
+
+
+def run_quality_grid(args):
+    """The plain FP32 method at paper-like scale: 5000 fixed passes (tol off)
+    on 256x256x128 and 512x512x224 cubes of the bench generator, for
+    sigma in {0.05, 0.1} x salt-and-pepper rate in {0.05, 0.1}, stripes on 10 %
+    of columns, dead lines on 2 % of columns in 10 % of bands.  Throughput
+    (CUDA events around gsstv_solve: state reset, the passes, the copy-out),
+    the scheduled iteration bandwidth, MPSNR and MSSIM (every 4th band)
+    against the clean cube.  One JSON line."""
+    import torch
+    from paper_2510_00562_gb300 import metrics, synth
+    from paper_2510_00562_gb300.solver import GeoSSTVSolver, make_params
+    iters = args.quality_iters
+    stream = torch.cuda.current_stream()
+    peak, src = measured_peaks()
+    rows = []
+    for n1, n2, n3 in QUALITY_SHAPES:
+        nvox = n1 * n2 * n3
+        with GeoSSTVSolver(n1, n2, n3, make_params(max_iter=iters, graph_iters=16), stream=stream) as sol:
+            for sg in QUALITY_SIGMAS:
+                for sp in QUALITY_SP:
+                    nz = synth.NoiseSpec(sigma=sg, sp_rate=sp, stripe_rate=0.1, stripe_amp=0.25,
+                                         dead_col_rate=0.02, dead_band_rate=0.1)
+                    pb = synth.make_problem(n1, n2, n3, seed=7, noise=nz)
+                    sol.set_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03)
+                    v = torch.from_numpy(pb["v"]).cuda()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    with ClockSampler(torch.cuda.current_device()) as clk:
+                        e0.record(stream)
+                        u, _, _, done = sol.solve(v)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    un = u.cpu().numpy()
+                    rows.append({
+                        "cube": f"{n1}x{n2}x{n3}", "sigma": sg, "sp_rate": sp, "passes": done,
+                        "seconds": ms / 1e3, "value": nvox * done / (ms * 1e-3), "unit": UNIT,
+                        "iteration_gbs": ITER_WORDS * 4 * nvox * done / (ms * 1e-3) / 1e9,
+                        "mpsnr_db": metrics.mpsnr(un, pb["u_bar"]),
+                        "mssim_every_4th_band": metrics.mssim(un[::4], pb["u_bar"][::4]),
+                        "observation_mpsnr_db": metrics.mpsnr(pb["v"], pb["u_bar"]),
+                        "clocks": clk.summary()})
+                    del v, u
+    print(json.dumps({"quality_grid": {"data": "synthetic", "storage": "fp32", "omega": 0.03,
+                                       "radii": "make_problem (rho 0.95, 0.9, 0.9)", "peak_gbs": peak,
+                                       "peak_source": src, "runs": rows}}), flush=True)
+    return 0
+
+
 # words per voxel of one transposed pass in place (k_adjoint.cu), every array
 # element read or written once per kernel: SUMS reads 10; CUBE reads 18
 # (states k and k+1 where q and the box need them, the adjoints of u, s, t,
@@ -710,6 +764,9 @@ def main(argv=None):
                     help="run only the omega sweep of the five noise cases on a cube of this size")
     ap.add_argument("--batch", type=int, default=0, metavar="NCUBES",
                     help="run only the batch measurement on NCUBES uneven cubes and print one JSON line")
+    ap.add_argument("--quality-grid", action="store_true",
+                    help="run only the 5000-pass quality grid on 256x256x128 and 512x512x224")
+    ap.add_argument("--quality-iters", type=int, default=5000)
     ap.add_argument("--grad", default=None, metavar="N1xN2xN3",
                     help="run only the reverse-mode measurement on a cube of this size")
     ap.add_argument("--grad-iters", type=int, default=200)
@@ -730,6 +787,8 @@ def main(argv=None):
         return run_omega_sweep(args)
     if args.grad:
         return run_grad(args)
+    if args.quality_grid:
+        return run_quality_grid(args)
     return run_gpu(args)
 
 
