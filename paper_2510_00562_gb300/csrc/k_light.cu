@@ -11,6 +11,7 @@
 // which the next iteration applies when it reads q.  It also reduces the two
 // norms of the stopping rule (Eq. 28).
 #include <algorithm>
+#include <type_traits>
 
 #include "gsstv_internal.cuh"
 #include "gsstv_l1.cuh"
@@ -521,22 +522,22 @@ __global__ void k_apply_flat(const float* x, float* out, long long n, const Scal
 // ---------------------------------------------------------------------------
 // layout conversion: (ncubes, n3, n1, *) arrays between pitches and types
 // ---------------------------------------------------------------------------
-// Row by row: blocks in y walk the rows of all cubes (one division per row),
-// threads in x the columns.
+// Cube by cube, 32 x 8 threads: a warp takes 32 columns of one row, blocks in
+// y walk the rows (no division per element).
 template <typename S, typename D>
-__global__ void k_convert(const S* src, long long src_pitch, long long src_cube, D* dst,
-                          long long dst_pitch, long long dst_cube, int n1, int n2, int n3,
-                          int ncubes, const double* scale) {
+__global__ void __launch_bounds__(256) k_convert(const S* src, long long src_pitch, long long src_cube, D* dst,
+                                                 long long dst_pitch, long long dst_cube, int n1, int n2, int n3,
+                                                 int ncubes, const double* scale) {
     const float f = scale ? (float)(1.0 - *scale) : 1.f;
     const long long rows = (long long)n3 * n1;
-    const long long total = rows * ncubes;
-    for (long long r = blockIdx.y; r < total; r += gridDim.y) {
-        const long long cb = r / rows, row = r - cb * rows;    // row = b * n1 + i
-        const S* s = src + cb * src_cube + row * src_pitch;
-        D* d = dst + cb * dst_cube + row * dst_pitch;
-        for (int j = blockIdx.x * NT + threadIdx.x; j < n2; j += gridDim.x * NT) {
-            const float x = ldT(s + j);
-            stT(d + j, scale ? f * x : x);
+    for (int cb = 0; cb < ncubes; ++cb) {
+        for (long long row = blockIdx.y * 8ll + threadIdx.y; row < rows; row += gridDim.y * 8ll) {
+            const S* s = src + cb * src_cube + row * src_pitch;
+            D* d = dst + cb * dst_cube + row * dst_pitch;
+            for (int j = blockIdx.x * 32 + threadIdx.x; j < n2; j += gridDim.x * 32) {
+                const float x = ldT(s + j);
+                stT(d + j, scale ? f * x : x);
+            }
         }
     }
 }
@@ -616,11 +617,18 @@ int launch_window_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal*
 template <typename S, typename D>
 int launch_convert(const S* src, long long sp, long long sc_, D* dst, long long dp, long long dc,
                    const Geom& g, int ncubes, const double* scale, cudaStream_t st) {
-    const long long rows = (long long)g.n3 * g.n1 * ncubes;
-    const int gx = (g.n2 + NT - 1) / NT;
-    const long long gy = std::max(1ll, std::min({rows, (152ll * 16) / gx, 65535ll}));
-    k_convert<S, D><<<dim3(gx, (unsigned)gy), NT, 0, st>>>(src, sp, sc_, dst, dp, dc, g.n1, g.n2, g.n3,
-                                                           ncubes, scale);
+    const long long rows = (long long)g.n3 * g.n1;
+    if constexpr (std::is_same<S, float>::value && std::is_same<D, float>::value) {
+        // float32 to float32 unscaled: one pitched copy of every row of every cube
+        if (!scale && sc_ == rows * sp && dc == rows * dp)
+            return cudaMemcpy2DAsync(dst, (size_t)dp * 4, src, (size_t)sp * 4, (size_t)g.n2 * 4,
+                                     (size_t)(rows * ncubes), cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                       ? 0 : -3;
+    }
+    const int gx = std::min((g.n2 + 31) / 32, 64);
+    const long long gy = std::max(1ll, std::min({(rows + 7) / 8, (152ll * 16) / gx, 65535ll}));
+    k_convert<S, D><<<dim3(gx, (unsigned)gy), dim3(32, 8), 0, st>>>(src, sp, sc_, dst, dp, dc, g.n1, g.n2, g.n3,
+                                                                    ncubes, scale);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
