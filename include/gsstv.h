@@ -212,7 +212,7 @@ int gsstv_batch_destroy(gsstv_batch* b);
  * place; no other views may overlap).  Adds the adjoint of v to d_vbar (N
  * floats) and those of (eps, alpha, beta, omega) to h_pbar[0..3] (host).
  * All views: float32 device arrays in the layout of gsstv_state_view.  Uses
- * a workspace of about 16 N floats held by the handle from the first call.
+ * a workspace of about 15 N floats held by the handle from the first call.
  * Synchronises the stream to read the parameter adjoints back; with h_pbar
  * NULL it skips them and returns once the work is queued.
  *
@@ -223,7 +223,7 @@ int gsstv_batch_destroy(gsstv_batch* b);
  * start u = v -- and to h_pbar[0..3] those of eps, alpha, beta, omega.
  * ckpt_every: passes between checkpoints (0 = ceil(sqrt(iters))); with
  * C = min(ckpt_every, iters) the call allocates ceil(iters/C) + C + 1 states
- * of 21 N floats and a 16 N-float workspace with cudaMalloc and frees them
+ * of 21 N floats and a 15 N-float workspace with cudaMalloc and frees them
  * before returning (GSSTV_ERR_OOM if they do not fit), runs the passes about
  * twice in all (once with ckpt_every = 1: every state is kept and nothing is
  * run again), and leaves the handle's state unspecified (reset it before

@@ -417,6 +417,14 @@ static bool view_ok(const gsstv_state_view* v) {
 // Unpacks the current state into float32 views on the handle's stream (no sync).
 static int enqueue_get_state(gsstv_handle* h, const gsstv_state_view* v) {
     const int par = h->parity, sto = h->p.storage;
+    {
+        const void* src[9] = {h->u[par], h->s[par], h->t[par], h->w1[par], h->w2[par],
+                              h->y1[par], h->y2[par], h->y3[par], h->q[par]};
+        float* dst[9] = {v->u, v->s, v->t, v->w1, v->w2, v->y1, v->y2, v->y3, v->y4};
+        const int rc = launch_unpack_state(sto, src, dst, &h->sc->c[par], h->g, h->st);
+        if (rc == 0) return GSSTV_OK;
+        if (rc != 1) return GSSTV_ERR_CUDA;
+    }
     TRY(map_launch(launch_unpack(sto, h->u[par], v->u, h->g, 1, h->st)));
     TRY(map_launch(launch_unpack(sto, h->s[par], v->s, h->g, 1, h->st)));
     TRY(map_launch(launch_unpack(sto, h->t[par], v->t, h->g, 1, h->st)));

@@ -312,6 +312,10 @@ int launch_pack(int storage, const float* src, void* dst, const Geom& g, int ncu
 int launch_pitched_to_storage(int storage, const float* src, void* dst, const Geom& g, cudaStream_t st);
 int launch_dense_to_pitched(const float* src, float* dst, const Geom& g, cudaStream_t st);
 int launch_unpack(int storage, const void* src, float* dst, const Geom& g, int ncubes, cudaStream_t st);
+// a whole state (u, s, t, w1, w2, y1, y2, y3, and y4 = (1 - *c) q) in one
+// launch; returns 1 when the storage or the row geometry does not allow it
+int launch_unpack_state(int storage, const void* const src[9], float* const dst[9], const double* c,
+                        const Geom& g, cudaStream_t st);
 int launch_scale_unpack(int storage, const void* q, const double* c, float* dst, const Geom& g,
                         cudaStream_t st);
 

@@ -562,6 +562,34 @@ __global__ void __launch_bounds__(256) k_convert4(const float4* src, long long s
     }
 }
 
+// All 21 float32 cubes of a state in one launch (grid z = cube), float4 rows;
+// the last cube (q) is scaled by 1 - c into y4.
+struct CubeCopy4 {
+    const float4* src;
+    float4* dst;
+    int scaled;
+};
+struct StateCopy4 {
+    CubeCopy4 c[21];
+    long long rows, src_pitch, dst_pitch;   // pitches in float4
+    int w4;
+    const double* scale;
+};
+
+__global__ void __launch_bounds__(256) k_unpack_state4(const StateCopy4 a) {
+    const CubeCopy4 cc = a.c[blockIdx.z];
+    const float f = cc.scaled ? (float)(1.0 - *a.scale) : 1.f;
+    for (long long row = blockIdx.y * 8ll + threadIdx.y; row < a.rows; row += gridDim.y * 8ll) {
+        const float4* s = cc.src + row * a.src_pitch;
+        float4* d = cc.dst + row * a.dst_pitch;
+        for (int j = blockIdx.x * 32 + threadIdx.x; j < a.w4; j += gridDim.x * 32) {
+            float4 x = __ldg(s + j);
+            if (cc.scaled) { x.x *= f; x.y *= f; x.z *= f; x.w *= f; }
+            d[j] = x;
+        }
+    }
+}
+
 int grid_for(long long n) {
     long long b = (n + NT - 1) / NT;
     return (int)std::max(1ll, std::min(b, 152ll * 16));
@@ -753,6 +781,32 @@ int launch_unpack(int storage, const void* src, float* dst, const Geom& g, int n
         case 2: return launch_convert((const __half*)src, g.p2, g.cube, dst, dp, dcb, g, ncubes, nullptr, st);
     }
     return -1;
+}
+
+int launch_unpack_state(int storage, const void* const src[9], float* const dst[9], const double* c,
+                        const Geom& g, cudaStream_t st) {
+    static const int ncubes[9] = {1, 1, 1, 6, 6, 2, 2, 1, 1};
+    if (storage != 0 || g.n2 % 4 != 0) return 1;
+    StateCopy4 a;
+    const long long dense = (long long)g.n3 * g.n1 * g.n2;
+    int k = 0;
+    for (int f = 0; f < 9; ++f) {
+        if (((reinterpret_cast<uintptr_t>(src[f]) | reinterpret_cast<uintptr_t>(dst[f])) & 15) != 0) return 1;
+        for (int cb = 0; cb < ncubes[f]; ++cb, ++k) {
+            a.c[k].src = reinterpret_cast<const float4*>(static_cast<const float*>(src[f]) + cb * g.cube);
+            a.c[k].dst = reinterpret_cast<float4*>(dst[f] + cb * dense);
+            a.c[k].scaled = f == 8;
+        }
+    }
+    a.rows = (long long)g.n3 * g.n1;
+    a.src_pitch = g.p2 / 4;
+    a.dst_pitch = g.n2 / 4;
+    a.w4 = g.n2 / 4;
+    a.scale = c;
+    const int gx = std::min((a.w4 + 31) / 32, 64);
+    const long long gy = std::max(1ll, std::min({(a.rows + 7) / 8, (152ll * 16) / (gx * 21ll), 65535ll}));
+    k_unpack_state4<<<dim3(gx, (unsigned)gy, 21), dim3(32, 8), 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int launch_scale_unpack(int storage, const void* q, const double* c, float* dst, const Geom& g,
