@@ -136,3 +136,55 @@ def test_unrolled_grad_checkpointing_changes_nothing():
         assert got[0] == ref[0]
         assert np.array_equal(got[1], ref[1])
         assert got[2] == ref[2]
+
+
+def _bad_l12(x, pbar, g):          # drops the rank-one term of the shrink Jacobian
+    nrm = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2)
+    act = nrm > g
+    safe = np.where(act, nrm, 1.0)
+    xbar = np.where(act[:, None], (1.0 - g / safe)[:, None] * pbar, 0.0)
+    return xbar, -float(np.where(act, ((x / safe[:, None]) * pbar).sum(axis=1), 0.0).sum())
+
+
+def _bad_l1(x, pbar, r):           # keeps the support but forgets the mean removal
+    if np.abs(x).sum() <= r:
+        return pbar.copy(), 0.0
+    _, tau = o.proj_l1ball(x, r)
+    act = np.abs(x) > tau
+    return np.where(act, pbar, 0.0), 0.0
+
+
+def _bad_l2(q, ybar, eps, g):      # treats the l2 step as a plain rescale
+    nq = float(np.sqrt(np.sum(q * q)))
+    if nq <= eps * g:
+        return np.zeros_like(q), 0.0
+    return (1.0 - eps * g / nq) * ybar, -g * float(np.sum(q / nq * ybar))
+
+
+def _bad_box(x, pbar, lo, hi):     # passes the adjoint through the clamp everywhere
+    return pbar.copy()
+
+
+@pytest.mark.parametrize("name,bad", [("_l12_vjp", _bad_l12), ("_l1_vjp", _bad_l1), ("_l2_vjp", _bad_l2),
+                                      ("_box_vjp", _bad_box)])
+def test_planted_mistakes_fail_the_differences(monkeypatch, name, bad):
+    """Each Jacobian of the reverse mode matters: replacing one by a plausible
+    wrong version breaks the agreement with central differences."""
+    shape = (4, 6, 5)
+    st, v = _random_point(shape, 0)
+    p = _params_for(st, v)
+    rng = np.random.default_rng(100)
+    out_w = o.State(**{k: rng.standard_normal(getattr(st, k).shape) for k in KEYS})
+    d = o.State(**{k: rng.standard_normal(getattr(st, k).shape) for k in KEYS})
+    dv = rng.standard_normal(shape)
+    h = 1e-6
+    fd = (_inner(out_w, o.ppds_step(_axpy(st, h, d), v + h * dv, p)) -
+          _inner(out_w, o.ppds_step(_axpy(st, -h, d), v - h * dv, p))) / (2 * h)
+
+    def an():
+        bar, vbar, _ = A.step_vjp(st, v, p, out_w)
+        return _inner(bar, d) + float(np.sum(vbar * dv))
+
+    assert an() == pytest.approx(fd, rel=1e-6, abs=1e-9)     # the real one agrees
+    monkeypatch.setattr(A, name, bad)
+    assert abs(an() - fd) > 1e-4 * abs(fd), name
