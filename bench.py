@@ -1,14 +1,19 @@
 """Throughput of the GeoSSTV P-PDS iteration (Algorithm 1) on GB300.
 
-A step is one full pass of Algorithm 1 over one cube (all five launches:
-fused stencil pass, the three radix passes and the gather of the exact l1
-search, light pass).  The workload is the 512 x 512 x 224 synthetic cube
+A step is one full pass of Algorithm 1 over one cube (all seven launches:
+fused stencil pass, retry window, the three radix passes and the gather of
+the exact l1 search, light pass; the search launches return at once when the
+fused pass's window found the thresholds).  The workload is the 512 x 512 x 224 synthetic cube
 (sigma 0.1, 5% salt and pepper, stripes on 10% of the columns, dead lines on
 2% of the columns of 10% of the bands), float32 iterates.  The state (about
 10 GB) is far larger than L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|bf16|fp16]
     python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Other measurements, one JSON line each (not bench lines): --quality-grid
+(5000 passes over a noise grid), --grad N1xN2xN3 (reverse mode), --batch N
+(uneven cubes), --omega-sweep N1xN2xN3, --precision-study N1xN2xN3.
 
 Multi-GPU (torchrun, one rank per GPU): every rank solves its own cube
 (replicas, weak scaling); ranks only meet for the barrier and the max-time
