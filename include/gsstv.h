@@ -156,6 +156,18 @@ int gsstv_get_stats(gsstv_handle* h, gsstv_stats* out);
 int gsstv_reset_stats(gsstv_handle* h);
 int gsstv_set_timing(gsstv_handle* h, int on);
 
+/* Picks the number of bands each CTA of the fused stencil kernel runs
+ * through by measurement: times that kernel (CUDA events) over `passes`
+ * passes from the standard start on the loaded observation for each of a few
+ * candidate run lengths (the wave/prologue model's choice and the next best by
+ * its estimate), keeps the fastest for this handle and resets the state.
+ * *chunk_out (may be NULL) receives the bands per CTA chosen, or 0 when the
+ * handle runs the cooperative kernel (16-bit storage), which has nothing to
+ * tune.  Results do not depend on the choice beyond the summation order of
+ * the l1 window statistics.  Synchronises the stream; the counters of
+ * gsstv_get_stats are left as they were. */
+int gsstv_autotune(gsstv_handle* h, int passes, int* chunk_out);
+
 /* Bytes the handle holds on the device. */
 int64_t gsstv_device_bytes(const gsstv_handle* h);
 

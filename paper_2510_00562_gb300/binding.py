@@ -73,6 +73,7 @@ _SIGS = {
     "gsstv_reset_stats": (c_int, [c_void_p]),
     "gsstv_set_timing": (c_int, [c_void_p, c_int]),
     "gsstv_device_bytes": (c_int64, [c_void_p]),
+    "gsstv_autotune": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
     "gsstv_project_l1ball": (c_int, [c_void_p, c_int64, c_double, c_void_p,
                                      ctypes.POINTER(c_double), c_void_p]),
     "gsstv_project_l1ball_noalloc": (c_int, [c_void_p, c_int64, c_double, c_void_p,
@@ -205,6 +206,14 @@ def gsstv_reset_stats(h):
 
 def gsstv_set_timing(h, on: bool):
     _check(load().gsstv_set_timing(h, 1 if on else 0), "gsstv_set_timing")
+
+
+def gsstv_autotune(h, passes: int = 20) -> int:
+    """Times the fused stencil kernel for a few band-run lengths and keeps the
+    fastest; returns the bands per CTA chosen (0: nothing to tune)."""
+    chunk = c_int(0)
+    _check(load().gsstv_autotune(h, passes, ctypes.byref(chunk)), "gsstv_autotune")
+    return chunk.value
 
 
 def gsstv_device_bytes(h) -> int:

@@ -42,6 +42,7 @@ struct gsstv_handle {
     int k1_ctas = 0;
     int parity = 0;               // ping-pong index that holds the current state
     int k1_variant = 1;           // 1: TMA-fed K1, 0: cooperative-load K1 (GSSTV_K1=coop)
+    int k1_chunk = 0;             // bands per K1 CTA (0: the wave/prologue model's choice)
     K1Maps maps[2];               // tensor maps of the buffers read at parity 0 / 1
     cudaGraphExec_t gexec[2]{};
     int graph_len = 0;
@@ -147,7 +148,7 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
         TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used], st)));
     }
     if (h->k1_variant == 1)
-        TRY(map_launch(launch_k1_tma(sto, h->g, h->maps[par], b, ip, h->sc, h->l1, st)));
+        TRY(map_launch(launch_k1_tma(sto, h->g, h->maps[par], b, ip, h->sc, h->l1, h->k1_chunk, st)));
     else
         TRY(map_launch(launch_k1(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, st)));
     if (timed) {
@@ -499,6 +500,46 @@ int gsstv_set_state(gsstv_handle* h, const gsstv_state_view* v) {
     TRY(map_launch(launch_pack(sto, v->y4, h->q[par], h->g, 1, h->st)));
     // y4 is now stored unscaled (c = 0); the threshold search starts afresh
     return upload_scalars(h, initial_scalars(h->p));
+}
+
+int gsstv_autotune(gsstv_handle* h, int passes, int* chunk_out) {
+    if (chunk_out) *chunk_out = 0;
+    if (!h || passes < 1) return GSSTV_ERR_ARG;
+    if (h->k1_variant != 1) return GSSTV_OK;          // the cooperative kernel has no run length to tune
+    int cand[6];
+    const int nc = k1_tma_chunk_candidates(h->g, cand, 6);
+    const gsstv_stats saved_stats = h->stats;
+    const int saved_timing = h->timing;
+    double best = INFINITY;
+    int best_chunk = 0;
+    int rc = flush_timing(h);
+    for (int k = 0; k < nc && rc == GSSTV_OK; ++k) {
+        h->k1_chunk = cand[k];
+        h->timing = 0;
+        rc = gsstv_reset_state(h);
+        if (rc == GSSTV_OK) rc = run_block(h, 1);     // untimed first pass
+        h->timing = 1;
+        const double ms0 = h->stats.k1_ms;
+        const int64_t n0 = h->stats.k1_launches;
+        if (rc == GSSTV_OK) rc = run_block(h, passes);
+        if (rc == GSSTV_OK) rc = flush_timing(h);
+        Scal sc;
+        if (rc == GSSTV_OK) rc = read_scalars(h, &sc);
+        if (rc == GSSTV_OK) rc = error_of(sc);
+        const int64_t n = h->stats.k1_launches - n0;
+        if (rc == GSSTV_OK && n > 0) {
+            const double ms = (h->stats.k1_ms - ms0) / (double)n;
+            if (ms < best) { best = ms; best_chunk = cand[k]; }
+        }
+    }
+    h->timing = saved_timing;
+    h->stats = saved_stats;
+    h->k1_chunk = rc == GSSTV_OK ? best_chunk : 0;
+    destroy_graphs(h);                                  // graphs hold the old launch shape
+    TRY(rc);
+    TRY(gsstv_reset_state(h));
+    if (chunk_out) *chunk_out = h->k1_chunk;
+    return GSSTV_OK;
 }
 
 int gsstv_get_stats(gsstv_handle* h, gsstv_stats* out) {

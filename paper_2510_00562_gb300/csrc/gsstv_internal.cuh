@@ -287,10 +287,12 @@ struct K1Maps {
 };
 
 int k1_tma_ctas(const Geom& g);
+int k1_tma_chunk_candidates(const Geom& g, int* out, int cap);
 int k1_tma_configure(int storage);
 int k1_tma_maps(int storage, const Geom& g, const IterBufs& b, K1Maps* m);
+// chunk: bands per CTA (0 or out of range: the wave/prologue model's choice)
 int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p,
-                  Scal* sc, const L1Work& w, cudaStream_t st);
+                  Scal* sc, const L1Work& w, int chunk, cudaStream_t st);
 
 int launch_k1(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
               const L1Work& w, int n_cta_slots, cudaStream_t st);

@@ -20,6 +20,7 @@
 // the 12 w planes (1-pixel halo, w' written in place) fit beside u' of three
 // bands and D^T y2 of the previous band: about 216 KB of shared memory.
 #include <algorithm>
+#include <vector>
 #include <cmath>
 #include <type_traits>
 
@@ -706,10 +707,38 @@ int tma_chunk(const Geom& g, int tiles) {
 
 }  // namespace
 
+// CTAs of the largest launch any allowed band run gives (runs of at least 8
+// bands, or all of them when there are fewer): the per-CTA statistics arrays
+// are sized for it.
 int k1_tma_ctas(const Geom& g) {
     const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
-    const int chunk = tma_chunk(g, tx * ty);
-    return tx * ty * ((g.n3 + chunk - 1) / chunk);
+    const int shortest = std::min(8, g.n3);
+    return tx * ty * ((g.n3 + shortest - 1) / shortest);
+}
+
+// Run lengths worth timing: the model's choice and the next best by its
+// estimate, at most `cap` distinct lengths, the model's choice first.
+int k1_tma_chunk_candidates(const Geom& g, int* out, int cap) {
+    constexpr double kSms = 152.0, kPrologue = 1.5;
+    const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
+    const int tiles = tx * ty;
+    const int max_chunks = std::max(1, g.n3 / 8);
+    std::vector<std::pair<double, int>> c;
+    for (int chunks = 1; chunks <= max_chunks; ++chunks) {
+        const int len = (g.n3 + chunks - 1) / chunks;
+        if (!c.empty() && c.back().second == len) continue;
+        const int used = (g.n3 + len - 1) / len;
+        const double units = (double)tiles * used;
+        const double waves = std::ceil(units / kSms);
+        c.push_back({(waves - units / kSms) / waves + kPrologue / len, len});
+    }
+    std::stable_sort(c.begin(), c.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    const int first = tma_chunk(g, tiles);
+    int n = 0;
+    if (cap > 0) out[n++] = first;
+    for (const auto& e : c)
+        if (n < cap && e.second != first) out[n++] = e.second;
+    return n;
 }
 
 // The TMA-fed kernel is built for float32 storage only (16-bit storage runs
@@ -738,7 +767,7 @@ int k1_tma_maps(int storage, const Geom& g, const IterBufs& b, K1Maps* m) {
 }
 
 int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p,
-                  Scal* sc, const L1Work& w, cudaStream_t st) {
+                  Scal* sc, const L1Work& w, int chunk, cudaStream_t st) {
     if (storage != 0) return -1;
     K1TArgs a;
     a.g = g;
@@ -748,7 +777,7 @@ int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b
     a.sc = sc;
     a.l1 = w;
     const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
-    a.chunk = tma_chunk(g, tx * ty);
+    a.chunk = chunk >= std::min(8, g.n3) && chunk <= g.n3 ? chunk : tma_chunk(g, tx * ty);
     dim3 grid(tx, ty, (g.n3 + a.chunk - 1) / a.chunk);
     k1_tma<<<grid, Lay::NT, Lay::SMEM, st>>>(m, a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;

@@ -160,6 +160,14 @@ class GeoSSTVSolver:
     def device_bytes(self) -> int:
         return B.gsstv_device_bytes(self.h)
 
+    def autotune(self, v: torch.Tensor | None = None, passes: int = 20) -> int:
+        """Measures the fused stencil kernel's band-run lengths on v (or the
+        loaded observation) and keeps the fastest; the state is reset.
+        Returns the bands per CTA chosen (0: nothing to tune)."""
+        if v is not None:
+            B.gsstv_load_observation(self.h, self._dev(v).data_ptr())
+        return B.gsstv_autotune(self.h, passes)
+
 
 class GeoSSTVBatch:
     """Independent cubes of different shapes solved together (libgsstv batch):
@@ -208,6 +216,20 @@ class GeoSSTVBatch:
         done = B.gsstv_batch_solve(self.b, [v.data_ptr() for v in vs], [u.data_ptr() for u in us],
                                    [s.data_ptr() for s in ss], [t.data_ptr() for t in ts])
         return us, ss, ts, done
+
+    def autotune(self, vs, passes: int = 20) -> list:
+        """Autotunes every cube's fused stencil kernel on its observation
+        (GeoSSTVSolver.autotune); returns the bands per CTA chosen."""
+        if len(vs) != len(self.shapes):
+            raise ValueError("one observation per cube")
+        out = []
+        for c, (v, shp) in enumerate(zip(vs, self.shapes)):
+            if tuple(v.shape) != shp or v.dtype != torch.float32 or not v.is_cuda or not v.is_contiguous():
+                raise ValueError(f"expected a contiguous float32 CUDA tensor of shape {shp}")
+            h = B.gsstv_batch_handle(self.b, c)
+            B.gsstv_load_observation(h, v.data_ptr())
+            out.append(B.gsstv_autotune(h, passes))
+        return out
 
     def stats(self, c: int) -> dict:
         s = B.gsstv_get_stats(B.gsstv_batch_handle(self.b, c))

@@ -73,6 +73,7 @@ def test_null_arguments(lib):
     acc = (ctypes.c_double * 4)()
     assert lib.gsstv_vjp_step(None, None, None, None, None, None, acc) == B.GSSTV_ERR_ARG
     assert lib.gsstv_unrolled_vjp(None, 1, 0, None, None, acc) == B.GSSTV_ERR_ARG
+    assert lib.gsstv_autotune(None, 1, None) == B.GSSTV_ERR_ARG
 
 
 def test_batch_rejects_bad_arguments_before_touching_the_device(lib):

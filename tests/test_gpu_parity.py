@@ -329,3 +329,25 @@ def test_oversized_cube_is_refused():
     with pytest.raises(B.GsstvError) as ei:
         GeoSSTVSolver(1 << 20, 1 << 14, 4096, make_params())
     assert ei.value.code == B.GSSTV_ERR_ARG
+
+
+def test_autotune_picks_a_valid_run_length_and_keeps_the_results():
+    """gsstv_autotune changes only how the fused kernel's CTAs split the
+    bands: the solve afterwards equals the one before up to the summation
+    order of the l1 window statistics, and still matches the oracle."""
+    n1, n2, n3, iters = 70, 100, 40, 60
+    pb = _problem(n1, n2, n3, seed=4)
+    v = to_dev(pb["v"])
+    p = make_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03, max_iter=iters)
+    with GeoSSTVSolver(n1, n2, n3, p) as sol:
+        u0, s0, t0, _ = sol.solve(v)
+        before = sol.stats()["iterations"]
+        chunk = sol.autotune(v, passes=4)
+        assert sol.stats()["iterations"] == before
+        assert 8 <= chunk <= n3
+        u1, s1, t1, n = sol.solve(v)
+    assert n == iters
+    for a, b in ((u1, u0), (s1, s0), (t1, t0)):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-6
+    st, _ = o.solve(pb["v"].astype(np.float64), oracle_params(p), iters)
+    assert rel(u1.cpu().numpy(), st.u) < 1e-5
