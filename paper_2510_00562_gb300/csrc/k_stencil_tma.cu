@@ -75,6 +75,10 @@ struct Lay {
     static constexpr int TY = 16, TX = 32, NT = 512;
     static constexpr int OX = 4;                   // left halo columns: boxes start 16-byte aligned
     static constexpr int SW = TX + 2 * OX;         // width of the staged planes
+    // the thread that issues the bulk copies: lane 0 of warp 8, a warp with no
+    // ring items (the ring warps are 0-7 and 11), so the serial copy issue
+    // does not lengthen the slowest warp of a band step
+    static constexpr int PRODUCER = 256;
     static constexpr int YR = TY + 4, WR = TY + 2, UR = TY + 1, UC = TX + 1;
     static constexpr int Y_B = pad128(YR * SW * 4);
     static constexpr int W_B = pad128(WR * SW * 4);
@@ -486,7 +490,7 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     };
 
     // ---- prologue: D^T y2 of band b0-1 and u' of band b0 ----
-    if (tid == 0) {
+    if (tid == L::PRODUCER) {
         for (int band = bstart; band <= min(bstart + L::NYS - 1, blast); ++band) issue_y(band);
         issue_w(b0);
         if (b0 + 1 < b1) issue_w(b0 + 1);
@@ -518,7 +522,7 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     float yprev[4] = {0.f, 0.f, 0.f, 0.f};
     auto step = [&](int b, auto do_t) -> bool {
         const bool has_next = b + 1 < g.n3;
-        if (tid == 0) {
+        if (tid == L::PRODUCER) {
             if (b + 2 <= blast && b + 2 - bstart >= L::NYS) issue_y(b + 2);
             if (b + 2 < b1) issue_w(b + 2);
         }
@@ -590,8 +594,9 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
                          : k1_tile<false>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs);
     if (!ok) {
         // a load never arrived: record it, let this CTA's copies land (bounded)
-        // before its shared memory is released, and skip the statistics
-        if (tid == 0) {
+        // before its shared memory is released, and skip the statistics (the
+        // producer holds the counts of the copies it issued)
+        if (tid == L::PRODUCER) {
             atomicOr(&a.sc->error, 4);
             for (int k = 0; k < L::NYS; ++k)
                 if (S.n_y > (unsigned)k) (void)mbar_wait(bars + k, ((S.n_y - 1 - k) / L::NYS) & 1);
