@@ -23,7 +23,7 @@ vertical component (located at (i+1/2, j)) and c = 1 the horizontal one (at
 (i, j+1/2)).  An auxiliary w in R^{6N} is ``w[g, c, b, i, j]`` with g = 0, 1, 2
 for the grids (i+1/2, j), (i, j+1/2), (i, j) of L_vert, L_hori, L_cent.
 
-Readings of the paper taken here (each one is listed in the design doc):
+Readings of the paper taken here:
 
 * D_v differentiates along rows i (vertical), D_h along columns j, D_s along
   bands b.  Sec. II-A names them "horizontal, vertical, spectral"; the
