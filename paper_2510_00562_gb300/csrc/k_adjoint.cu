@@ -484,20 +484,11 @@ __global__ void __launch_bounds__(256) k_axpy(float* y, const float* x, float a,
         y[l] += a * x[l];
 }
 
-// blocks of 32 x 8 threads: columns in x, persistent over the rows in y
-dim3 adj_grid(const Dims& d, int resident) {
-    const int gx = (d.n2 + BX - 1) / BX;
-    const long long rb = ((long long)d.rows + BY - 1) / BY;
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-            sms = 152;
-    }
-    const long long want = std::max(1ll, (long long)sms * std::max(1, resident) / gx);
-    return dim3(gx, (unsigned)std::min({rb, want, 65535ll}));
-}
+// Launch facts of one device: SM count and resident blocks of each kernel.
+struct AdjInfo {
+    int sms = 0;
+    int res[5] = {0, 0, 0, 0, 0};
+};
 
 int resident_of(const void* fn) {
     int nb = 0;
@@ -506,6 +497,44 @@ int resident_of(const void* fn) {
         return 1;
     }
     return std::max(1, nb);
+}
+
+// Filled on the first launch with each device current (ordinals below 64;
+// concurrent first launches write the same values).
+const AdjInfo& adj_info();
+
+// blocks of 32 x 8 threads: columns in x, persistent over the rows in y
+dim3 adj_grid(const Dims& d, int resident, int sms) {
+    const int gx = (d.n2 + BX - 1) / BX;
+    const long long rb = ((long long)d.rows + BY - 1) / BY;
+    const long long want = std::max(1ll, (long long)sms * std::max(1, resident) / gx);
+    return dim3(gx, (unsigned)std::min({rb, want, 65535ll}));
+}
+
+const AdjInfo& adj_info() {
+    constexpr int kMaxDev = 64;
+    static AdjInfo info[kMaxDev];
+    static AdjInfo fallback;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    AdjInfo& a = dev >= 0 && dev < kMaxDev ? info[dev] : fallback;
+    if (a.sms == 0) {
+        int sms = 0;
+        if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            sms = 152;
+        }
+        a.res[0] = resident_of((const void*)k_adj_sums);
+        a.res[1] = resident_of((const void*)k_adj_cube);
+        a.res[2] = resident_of((const void*)k_adj_aux);
+        a.res[3] = resident_of((const void*)k_adj_fin1);
+        a.res[4] = resident_of((const void*)k_adj_fin2);
+        a.sms = sms;
+    }
+    return a;
 }
 
 }  // namespace
@@ -524,14 +553,8 @@ size_t adjoint_workspace_bytes(long long n) {
 int launch_adjoint_step(int n1, int n2, int n3, const float* const x[9], const float* const x1[9],
                         const float* const b1[9], float* const bo[9], const float* v, int v_pitch,
                         float* vbar, double* pbar, void* work, const double prm[16], cudaStream_t st) {
-    static int res[5] = {0, 0, 0, 0, 0};
-    if (res[0] == 0) {
-        res[1] = resident_of((const void*)k_adj_cube);
-        res[2] = resident_of((const void*)k_adj_aux);
-        res[3] = resident_of((const void*)k_adj_fin1);
-        res[4] = resident_of((const void*)k_adj_fin2);
-        res[0] = resident_of((const void*)k_adj_sums);
-    }
+    const AdjInfo& info = adj_info();
+    const int* res = info.res;
     AdjArgs a;
     a.d.n1 = n1; a.d.n2 = n2; a.d.n3 = n3; a.d.vp = v_pitch;
     a.d.rows = n3 * n1;
@@ -563,11 +586,11 @@ int launch_adjoint_step(int n1, int n2, int n3, const float* const x[9], const f
     if (N == 0) return 0;
     if (cudaMemsetAsync(a.sc, 0, NSCAL * sizeof(double), st) != cudaSuccess) return -3;
     const dim3 blk(BX, BY);
-    k_adj_sums<<<adj_grid(a.d, res[0]), blk, 0, st>>>(a);
-    k_adj_cube<<<adj_grid(a.d, res[1]), blk, 0, st>>>(a);
-    k_adj_aux<<<adj_grid(a.d, res[2]), blk, 0, st>>>(a);
-    k_adj_fin1<<<adj_grid(a.d, res[3]), blk, 0, st>>>(a);
-    k_adj_fin2<<<adj_grid(a.d, res[4]), blk, 0, st>>>(a);
+    k_adj_sums<<<adj_grid(a.d, res[0], info.sms), blk, 0, st>>>(a);
+    k_adj_cube<<<adj_grid(a.d, res[1], info.sms), blk, 0, st>>>(a);
+    k_adj_aux<<<adj_grid(a.d, res[2], info.sms), blk, 0, st>>>(a);
+    k_adj_fin1<<<adj_grid(a.d, res[3], info.sms), blk, 0, st>>>(a);
+    k_adj_fin2<<<adj_grid(a.d, res[4], info.sms), blk, 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
