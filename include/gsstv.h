@@ -156,8 +156,9 @@ int gsstv_get_stats(gsstv_handle* h, gsstv_stats* out);
 int gsstv_reset_stats(gsstv_handle* h);
 int gsstv_set_timing(gsstv_handle* h, int on);
 
-/* Picks the number of bands each CTA of the fused stencil kernel runs
- * through by measurement: times that kernel (CUDA events) over `passes`
+/* Launch tuning (the paper has no counterpart: this is a launch parameter of
+ * this implementation, not part of Algorithm 1).  Picks the number of bands
+ * each CTA of the fused stencil kernel runs through by measurement: times that kernel (CUDA events) over `passes`
  * passes from the standard start on the loaded observation for each of a few
  * candidate run lengths (the wave/prologue model's choice and the next best by
  * its estimate), keeps the fastest for this handle and resets the state.
