@@ -75,12 +75,18 @@ def test_batch_matches_oracle():
     vs = [torch.from_numpy(pb["v"]).cuda() for pb in pbs]
     with GeoSSTVBatch(shapes, params) as bt:
         us, ss, ts, done = bt.solve(vs)
-    assert done == iters
+        # every cube's fused kernel autotuned: the results stay within parity
+        chunks = bt.autotune(vs, passes=3)
+        us_t, ss_t, ts_t, done_t = bt.solve(vs)
+    assert done == iters and done_t == iters
+    for (n1, n2, n3), c in zip(shapes, chunks):
+        assert min(8, n3) <= c <= n3, (n3, c)
     for k, pb in enumerate(pbs):
         p = params[k]
         st, _ = o.solve(pb["v"].astype(np.float64), o.Params(eps=p.eps, alpha=p.alpha, beta=p.beta,
                                                              omega=p.omega), iters[k])
-        for got, ref in ((us[k], st.u), (ss[k], st.s), (ts[k], st.t)):
+        for got, ref in ((us[k], st.u), (ss[k], st.s), (ts[k], st.t), (us_t[k], st.u), (ss_t[k], st.s),
+                         (ts_t[k], st.t)):
             e = rel(got.cpu().numpy(), ref)
             print(f"batch cube {k} vs oracle: {e:.3e}")
             assert e < 1e-5
