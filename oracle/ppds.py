@@ -55,7 +55,7 @@ __all__ = [
     "Dv", "Dv_T", "Dh", "Dh_T", "Ds", "Ds_T", "D", "D_T",
     "shift", "L", "L_T",
     "prox_l12", "proj_box", "proj_l1ball", "proj_l2ball",
-    "init_state", "ppds_step", "solve",
+    "init_state", "ppds_step", "rel_change", "solve",
     "apply_A", "apply_AT", "geosstv_objective",
 ]
 
@@ -315,59 +315,70 @@ def init_state(v):
 
 
 def ppds_step(st: State, v, p: Params) -> State:
-    """One pass of the loop of Algorithm 1 (the P-PDS solver of Prob. 20).
+    """One pass of Algorithm 1: the P-PDS of Eq. 7 applied to Prob. 20.
 
-    Primal updates use the old duals; the duals use the extrapolated primals
-    x' = 2 x^(k+1) - x^(k).  y1, y2, y3 are plain ascent steps (the prox of the
-    indicator of {0} is 0, Eq. 22, through Moreau's identity Eq. 3); y4 takes
-    the l2-ball step y4' - gamma P_B(y4' / gamma) (Eq. 23).
+    Prob. 20 stacks the primal x = (u, w1, w2, s, t) and the dual
+    y = (y1, y2, y3, y4) through the operator A of ``apply_A``.  One pass is
+    x+ = prox_{Gamma1 f}(x - Gamma1 A^T y) block by block (box, Eq. 21; group
+    soft-threshold, Eq. 24; l1-ball projections, Sec. III-B), the
+    extrapolation x' = 2 x+ - x, and y+ = prox_{Gamma2 g*}(y + Gamma2 A x').
+    The dual blocks: g is the indicator of {0} for y1, y2, y3, so the prox of
+    its conjugate is the plain ascent (Eq. 22 through Moreau's identity,
+    Eq. 3); for y4 it is the indicator of B_{2,eps}^v, whose conjugate prox
+    is z - gamma P_B(z / gamma) (Eq. 23 through Eq. 3).  Dual steps take the
+    "+" sign of Algorithm 1.
     """
     v = np.asarray(v, dtype=np.float64)
-    # primal steps
-    u1 = proj_box(st.u - p.gamma_u * (D_T(st.y1) + Ds_T(D_T(st.y2)) + st.y4), p.mu_lo, p.mu_hi)
-    s1, tau_s = proj_l1ball(st.s - p.gamma_s * st.y4, p.alpha)
-    t1, tau_t = proj_l1ball(st.t - p.gamma_t * (Dv_T(st.y3) + st.y4), p.beta)
-    w11 = prox_l12(st.w1 + p.gamma_w1 * L(st.y1), p.gamma_w1 * p.omega)
-    w21 = prox_l12(st.w2 + p.gamma_w2 * L(st.y2), p.gamma_w2)
-    # extrapolation
-    ub = 2 * u1 - st.u
-    sb = 2 * s1 - st.s
-    tb = 2 * t1 - st.t
-    w1b = 2 * w11 - st.w1
-    w2b = 2 * w21 - st.w2
-    # dual steps
-    y11 = st.y1 + p.gamma_y1 * (D(ub) - L_T(w1b))
-    y21 = st.y2 + p.gamma_y2 * (D(Ds(ub)) - L_T(w2b))
-    y31 = st.y3 + p.gamma_y3 * Dv(tb)
-    y4p = st.y4 + p.gamma_y4 * (ub + sb + tb)
+    # primal blocks: x - Gamma1 A^T y, then the prox of each block of f
+    gu, gw1, gw2, gs, gt = apply_AT(st.y1, st.y2, st.y3, st.y4)
+    u1 = proj_box(st.u - p.gamma_u * gu, p.mu_lo, p.mu_hi)
+    w11 = prox_l12(st.w1 - p.gamma_w1 * gw1, p.gamma_w1 * p.omega)
+    w21 = prox_l12(st.w2 - p.gamma_w2 * gw2, p.gamma_w2)
+    s1, tau_s = proj_l1ball(st.s - p.gamma_s * gs, p.alpha)
+    t1, tau_t = proj_l1ball(st.t - p.gamma_t * gt, p.beta)
+    # extrapolated primal x' = 2 x+ - x
+    xb = [2 * a - b for a, b in ((u1, st.u), (w11, st.w1), (w21, st.w2), (s1, st.s), (t1, st.t))]
+    # dual blocks: y + Gamma2 A x', then the prox of each block of g*
+    a1, a2, a3, a4 = apply_A(*xb)
+    y11 = st.y1 + p.gamma_y1 * a1
+    y21 = st.y2 + p.gamma_y2 * a2
+    y31 = st.y3 + p.gamma_y3 * a3
+    y4p = st.y4 + p.gamma_y4 * a4
     y41 = y4p - p.gamma_y4 * proj_l2ball(y4p / p.gamma_y4, v, p.eps)
     out = State(u=u1, s=s1, t=t1, w1=w11, w2=w21, y1=y11, y2=y21, y3=y31, y4=y41)
     out.extra = {"tau_s": tau_s, "tau_t": tau_t}
     return out
 
 
-def solve(v, p: Params, iters: int, state: State | None = None, tol: float = 0.0):
-    """Run Algorithm 1 for ``iters`` passes (or until Eq. 28 holds when tol > 0).
+def rel_change(u_next, u_prev):
+    """The ratio of the stopping rule, Eq. 28: ||u^(k+1) - u^(k)||_2 / ||u^(k)||_2.
 
-    Eq. 28 stops when ||u^(k+1) - u^(k)||_2 / ||u^(k)||_2 < tol.
-    Returns (state, iterations done).
+    +inf when u^(k) = 0 (the ratio is undefined there and never stops the run).
+    """
+    den = np.linalg.norm(u_prev)
+    if den == 0:
+        return np.inf
+    return float(np.linalg.norm(u_next - u_prev) / den)
+
+
+def solve(v, p: Params, iters: int, state: State | None = None, tol: float = 0.0):
+    """Run Algorithm 1 for ``iters`` passes, or until Eq. 28 holds when tol > 0.
+
+    With tol > 0 the run stops after the first pass k + 1 whose ratio
+    ``rel_change(u^(k+1), u^(k))`` is below tol.  Returns (state, passes run).
     """
     st = init_state(v) if state is None else state.copy()
     for k in range(iters):
         nxt = ppds_step(st, v, p)
-        if tol > 0:
-            num = np.linalg.norm(nxt.u - st.u)
-            den = np.linalg.norm(st.u)
-            st = nxt
-            if den > 0 and num / den < tol:
-                return st, k + 1
-        else:
-            st = nxt
+        stop = tol > 0 and rel_change(nxt.u, st.u) < tol
+        st = nxt
+        if stop:
+            return st, k + 1
     return st, iters
 
 
 # ---------------------------------------------------------------------------
-# The stacked operator A of Prob. 20 and the GeoSSTV objective (tests only)
+# The stacked operator A of Prob. 20 (used by ppds_step) and the GeoSSTV objective
 # ---------------------------------------------------------------------------
 def apply_A(u, w1, w2, s, t):
     """A x = (D u - L^T w1, D D_s u - L^T w2, D_v t, u + s + t)  (Eq. 20)."""
