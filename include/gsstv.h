@@ -109,7 +109,10 @@ typedef struct gsstv_state_view {
  * storage FP32, tau_mode AUTO, graph_iters = 16. */
 void gsstv_default_params(gsstv_params* p);
 
-/* Creates a solver for N1 x N2 x N3 cubes.  Allocates and zeroes the whole
+/* Creates a solver for N1 x N2 x N3 cubes: the iterates of Algorithm 1
+ * (primal u, s, t, w1, w2 and dual y1..y4 of Prob. 20, Sec. III-A/III-B,
+ * with the sizes Eq. 13 gives them: w1, w2 in R^{6N}, y1, y2 in R^{2N}).
+ * Allocates and zeroes the whole
  * iterate state on the current device (about 43 cube-sized buffers of the
  * storage type plus a float32 copy of v).  stream: cudaStream_t or NULL.
  * Limits: N1, N2 <= 2^20, N3 <= 2^16 and 6 * N1 * N3 * (N2 rounded up to 8)
@@ -145,8 +148,13 @@ int gsstv_solve(gsstv_handle* h, const float* d_v, float* d_u, float* d_s,
 int gsstv_solve_host(gsstv_handle* h, const float* h_v, float* h_u, float* h_s,
                      float* h_t, int* iters_done);
 
-/* Reads / writes the full state through float32 device views (every pointer
- * non-NULL).  With 16-bit storage the values are rounded on write. */
+/* Reads / writes the full state of Algorithm 1 -- its primal iterates u, s, t,
+ * w1, w2 and dual iterates y1..y4 (Sec. III-B; the layout of
+ * gsstv_state_view) -- through float32 device views (every pointer non-NULL),
+ * for warm starts (Algorithm 1 takes its initial point as an input) and
+ * checkpoints.  With 16-bit storage the values are rounded on write.
+ * set_state restarts the l1 threshold search; the next pass continues
+ * Algorithm 1 from the given point. */
 int gsstv_get_state(gsstv_handle* h, const gsstv_state_view* st);
 int gsstv_set_state(gsstv_handle* h, const gsstv_state_view* st);
 

@@ -264,6 +264,10 @@ __device__ __forceinline__ void append_candidate(bool take, float x, float* cand
 // ---------------------------------------------------------------------------
 // kernel launchers (host)
 // ---------------------------------------------------------------------------
+// Streaming multiprocessors of the current device, queried once per device
+// (grids are sized in multiples of it).
+int device_sms();
+
 struct IterBufs {
     // current (read) and next (write) buffers of one iteration parity
     const void *u, *s, *t, *y3, *q, *w1, *w2, *y1, *y2;

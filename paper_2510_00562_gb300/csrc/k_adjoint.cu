@@ -43,6 +43,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "gsstv_internal.cuh"
@@ -511,29 +512,27 @@ dim3 adj_grid(const Dims& d, int resident, int sms) {
     return dim3(gx, (unsigned)std::min({rb, want, 65535ll}));
 }
 
+// Resident blocks of each kernel and the SM count, filled once per device
+// (std::call_once: concurrent first calls from several host threads wait for
+// the one that fills it).
 const AdjInfo& adj_info() {
     constexpr int kMaxDev = 64;
-    static AdjInfo info[kMaxDev];
-    static AdjInfo fallback;
+    static AdjInfo info[kMaxDev + 1];          // the last entry: device query failed
+    static std::once_flag once[kMaxDev + 1];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
         cudaGetLastError();
-        dev = -1;
+        dev = kMaxDev;
     }
-    AdjInfo& a = dev >= 0 && dev < kMaxDev ? info[dev] : fallback;
-    if (a.sms == 0) {
-        int sms = 0;
-        if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
-            cudaGetLastError();
-            sms = 152;
-        }
+    AdjInfo& a = info[dev];
+    std::call_once(once[dev], [&a] {
         a.res[0] = resident_of((const void*)k_adj_sums);
         a.res[1] = resident_of((const void*)k_adj_cube);
         a.res[2] = resident_of((const void*)k_adj_aux);
         a.res[3] = resident_of((const void*)k_adj_fin1);
         a.res[4] = resident_of((const void*)k_adj_fin2);
-        a.sms = sms;
-    }
+        a.sms = device_sms();
+    });
     return a;
 }
 
@@ -541,7 +540,7 @@ const AdjInfo& adj_info() {
 
 int launch_axpy(float* y, const float* x, float a, long long n, cudaStream_t st) {
     if (n <= 0) return 0;
-    const int grid = (int)std::min((n + 255) / 256, 152ll * 8);
+    const int grid = (int)std::min((n + 255) / 256, device_sms() * 8ll);
     k_axpy<<<grid, 256, 0, st>>>(y, x, a, n);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

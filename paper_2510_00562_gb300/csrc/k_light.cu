@@ -12,6 +12,7 @@
 // norms of the stopping rule (Eq. 28).
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "gsstv_internal.cuh"
@@ -592,7 +593,7 @@ __global__ void __launch_bounds__(256) k_unpack_state4(const StateCopy4 a) {
 
 int grid_for(long long n) {
     long long b = (n + NT - 1) / NT;
-    return (int)std::max(1ll, std::min(b, 152ll * 16));
+    return (int)std::max(1ll, std::min(b, device_sms() * 16ll));
 }
 
 template <typename T>
@@ -616,7 +617,7 @@ int launch_radix_src(const Src& src, long long n, const SearchArgs& a, int level
     const size_t smem = 6 * kHistBins * sizeof(unsigned);
     // enough CTAs that none sees more than 2^21 values (the shared bins are 32-bit)
     const long long min_ctas = (n + (1ll << 21) - 1) >> 21;
-    const int grid = (int)std::max<long long>(std::min(grid_for(n), 152 * 3), min_ctas);
+    const int grid = (int)std::max<long long>(std::min(grid_for(n), device_sms() * 3), min_ctas);
     k_radix<Src><<<grid, NT, smem, st>>>(src, a, level);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -647,7 +648,7 @@ int launch_gather_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal*
     SearchArgs a{sc, w, 2};
     const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc);
     const long long n = (long long)g.n3 * g.n1 * g.n2;
-    k_gather<CubeSrc<T>><<<std::min(grid_for(n), 152 * 4), NT, 0, st>>>(src, a);
+    k_gather<CubeSrc<T>><<<std::min(grid_for(n), device_sms() * 4), NT, 0, st>>>(src, a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -657,7 +658,7 @@ int launch_window_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal*
     SearchArgs a{sc, w, 2};
     const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc);
     const long long n = (long long)g.n3 * g.n1 * g.n2;
-    const int grid = std::max(1, std::min({grid_for(n), 152 * 4, part_cap}));
+    const int grid = std::max(1, std::min({grid_for(n), device_sms() * 4, part_cap}));
     k_window<CubeSrc<T>><<<grid, NT, 0, st>>>(src, a, w.k1_n, w.k1_s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -671,7 +672,7 @@ int launch_convert(const S* src, long long sp, long long sc_, D* dst, long long 
         if (a16 && sp % 4 == 0 && dp % 4 == 0 && sc_ % 4 == 0 && dc % 4 == 0 && g.n2 % 4 == 0) {
             const int w4 = g.n2 / 4;
             const int gx = std::min((w4 + 31) / 32, 64);
-            const long long gy = std::max(1ll, std::min({(rows + 7) / 8, (152ll * 16) / gx, 65535ll}));
+            const long long gy = std::max(1ll, std::min({(rows + 7) / 8, (device_sms() * 16ll) / gx, 65535ll}));
             k_convert4<<<dim3(gx, (unsigned)gy), dim3(32, 8), 0, st>>>(
                 reinterpret_cast<const float4*>(src), sp / 4, sc_ / 4, reinterpret_cast<float4*>(dst), dp / 4,
                 dc / 4, rows, w4, ncubes, scale);
@@ -679,13 +680,34 @@ int launch_convert(const S* src, long long sp, long long sc_, D* dst, long long 
         }
     }
     const int gx = std::min((g.n2 + 31) / 32, 64);
-    const long long gy = std::max(1ll, std::min({(rows + 7) / 8, (152ll * 16) / gx, 65535ll}));
+    const long long gy = std::max(1ll, std::min({(rows + 7) / 8, (device_sms() * 16ll) / gx, 65535ll}));
     k_convert<S, D><<<dim3(gx, (unsigned)gy), dim3(32, 8), 0, st>>>(src, sp, sc_, dst, dp, dc, g.n1, g.n2, g.n3,
                                                                     ncubes, scale);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 }  // namespace
+
+int device_sms() {
+    constexpr int kMaxDev = 64;
+    constexpr int kFallback = 152;     // GB300, if the query fails
+    static std::once_flag once[kMaxDev];
+    static int sms[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return kFallback;
+    }
+    std::call_once(once[dev], [dev] {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = kFallback;
+        }
+        sms[dev] = n;
+    });
+    return sms[dev];
+}
 
 int light_configure(int storage) {
     const int smem = 6 * kHistBins * sizeof(unsigned);
@@ -804,7 +826,7 @@ int launch_unpack_state(int storage, const void* const src[9], float* const dst[
     a.w4 = g.n2 / 4;
     a.scale = c;
     const int gx = std::min((a.w4 + 31) / 32, 64);
-    const long long gy = std::max(1ll, std::min({(a.rows + 7) / 8, (152ll * 16) / (gx * 21ll), 65535ll}));
+    const long long gy = std::max(1ll, std::min({(a.rows + 7) / 8, (device_sms() * 16ll) / (gx * 21ll), 65535ll}));
     k_unpack_state4<<<dim3(gx, (unsigned)gy, 21), dim3(32, 8), 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -849,7 +871,7 @@ int l1_project_standalone(const float* x, long long n, double radius, float* out
         const SearchArgs a{sc, w, 1};
         for (int level = 0; level < 3 && rc == 0; ++level) rc = launch_radix_src(src, n, a, level, st);
         if (rc == 0) {
-            k_gather<FlatSrc><<<std::min(grid_for(n), 152 * 4), NT, 0, st>>>(src, a);
+            k_gather<FlatSrc><<<std::min(grid_for(n), device_sms() * 4), NT, 0, st>>>(src, a);
             k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
             if (cudaGetLastError() != cudaSuccess) rc = -3;
         }
@@ -947,7 +969,7 @@ int l1_project_noalloc(const float* x, long long n, double radius, float* out, d
     const SearchArgs a{sc, w, 1};
     for (int level = 0; level < 3; ++level)
         if (launch_radix_src(src, n, a, level, st) != 0) return -3;
-    k_gather<FlatSrc><<<std::min(grid_for(n), 152 * 4), NT, 0, st>>>(src, a);
+    k_gather<FlatSrc><<<std::min(grid_for(n), device_sms() * 4), NT, 0, st>>>(src, a);
     k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
     if (cudaGetLastError() != cudaSuccess) return -3;
     double t = 0.0;

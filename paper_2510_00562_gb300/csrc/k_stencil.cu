@@ -431,7 +431,8 @@ int launch_k1_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
     a.sc = sc;
     a.l1 = w;
     const int tiles = ((g.n2 + TX - 1) / TX) * ((g.n1 + TY - 1) / TY);
-    int chunks = (2432 + tiles - 1) / tiles;               // about 16 CTAs per SM
+    const int target = device_sms() * 16;                  // about 16 CTAs per SM
+    int chunks = (target + tiles - 1) / tiles;
     chunks = max(1, min(chunks, (g.n3 + 7) / 8));          // at least 8 bands per CTA
     a.chunk = (g.n3 + chunks - 1) / chunks;
     chunks = (g.n3 + a.chunk - 1) / a.chunk;
@@ -455,7 +456,8 @@ int k1_configure(int storage) {
 
 int k1_grid_ctas(const Geom& g) {
     const int tiles = ((g.n2 + TX - 1) / TX) * ((g.n1 + TY - 1) / TY);
-    int chunks = (2432 + tiles - 1) / tiles;
+    const int target = device_sms() * 16;
+    int chunks = (target + tiles - 1) / tiles;
     chunks = std::max(1, std::min(chunks, (g.n3 + 7) / 8));
     const int chunk = (g.n3 + chunks - 1) / chunks;
     chunks = (g.n3 + chunk - 1) / chunk;

@@ -689,13 +689,14 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     if (tid == 0) a.sc->k1_ticket = 0;
 }
 
-// Bands per CTA.  One CTA runs per SM, so a launch of U CTAs takes
-// ceil(U / 152) waves and the last wave leaves SMs idle; every CTA also pays a
+// Bands per CTA.  One CTA runs per SM, so a launch of U CTAs on S SMs takes
+// ceil(U / S) waves and the last wave leaves SMs idle; every CTA also pays a
 // prologue of about 1.5 band steps (its first copies, D^T y2 of the band
 // before, u' of its first band).  Picks the split of the bands (runs of at
 // least 8) that minimises idle fraction + prologue fraction.
 int tma_chunk(const Geom& g, int tiles) {
-    constexpr double kSms = 152.0, kPrologue = 1.5;
+    const double kSms = (double)device_sms();
+    constexpr double kPrologue = 1.5;
     const int max_chunks = std::max(1, g.n3 / 8);
     int best_len = g.n3;
     double best = 1e30;
@@ -724,7 +725,8 @@ int k1_tma_ctas(const Geom& g) {
 // Run lengths worth timing: the model's choice and the next best by its
 // estimate, at most `cap` distinct lengths, the model's choice first.
 int k1_tma_chunk_candidates(const Geom& g, int* out, int cap) {
-    constexpr double kSms = 152.0, kPrologue = 1.5;
+    const double kSms = (double)device_sms();
+    constexpr double kPrologue = 1.5;
     const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
     const int tiles = tx * ty;
     const int max_chunks = std::max(1, g.n3 / 8);

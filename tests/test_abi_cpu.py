@@ -100,3 +100,12 @@ def test_batch_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.gsstv_batch_destroy(None) == B.GSSTV_OK
     assert lib.gsstv_batch_size(None) == 0
     assert lib.gsstv_batch_handle(None, 0, ctypes.byref(b)) == B.GSSTV_ERR_ARG
+
+
+def test_noalloc_limit_in_binding_matches_header():
+    # the binding checks sizes against its own copy of GSSTV_NOALLOC_MAX_N;
+    # it must be the header's value
+    src = open(HEADER).read()
+    m = re.search(r"#define\s+GSSTV_NOALLOC_MAX_N\s+(\d+)", src)
+    assert m is not None
+    assert int(m.group(1)) == B.GSSTV_NOALLOC_MAX_N

@@ -1,13 +1,17 @@
-"""The allocation-free l1-ball projection against the allocating one.
+"""The allocation-free l1-ball projection against the allocating one and the
+FP64 oracle.
 
 gsstv_project_l1ball_noalloc serves callers that must not allocate device
 memory (their memory belongs to another allocator, or cudaFree's device-wide
 synchronisation is not acceptable where they run): it keeps its scratch in a
 static device array.  It must give the same projection as
-gsstv_project_l1ball, call after call, since every call reuses (and must
-first clear) that shared array.  This file is collected last, so a failure
-here comes after every other test has run; it also passes on its own in a
-fresh process, where its first call is the one that sets the array up.
+gsstv_project_l1ball and as the oracle's sort-based projection (Sec. III-B),
+call after call, since every call reuses (and must first clear) that shared
+array.  The largest accepted size is run with every value equal and with
+values a few ulps apart, so that the radix search's bracket holds the whole
+input.  This file is collected last, so a failure here comes after every
+other test has run; it also passes on its own in a fresh process, where its
+first call is the one that sets the array up.
 """
 import ctypes
 
@@ -15,6 +19,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import ppds as o
 from paper_2510_00562_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
@@ -36,9 +41,14 @@ def _both(x, r):
 
 def _check(x, r):
     tau_ref, out_ref, tau_na, out_na = _both(x, r)
-    # the tolerances of the l1-projection parity tests
+    # the tolerances of the l1-projection parity tests, against the allocating
+    # projection and against the oracle
+    scale = 1e-6 * max(1.0, float(np.abs(x).max()))
     assert tau_na == pytest.approx(tau_ref, rel=1e-6, abs=1e-12)
-    assert np.abs(out_na - out_ref).max() <= 1e-6 * max(1.0, float(np.abs(x).max()))
+    assert np.abs(out_na - out_ref).max() <= scale
+    ref, tau_o = o.proj_l1ball(x.astype(np.float64), r)
+    assert tau_na == pytest.approx(tau_o, rel=1e-6, abs=1e-12)
+    assert np.abs(out_na - ref).max() <= scale
 
 
 def test_noalloc_matches_allocating_projection_two_calls_in_a_row():
@@ -54,6 +64,26 @@ def test_noalloc_matches_allocating_projection_two_calls_in_a_row():
     x3 = rng.uniform(-1, 1, size=1000).astype(np.float32)
     _check(x3, 10.0 * float(np.abs(x3.astype(np.float64)).sum()))
     _check(x3, 0.0)
+
+
+def test_noalloc_bracket_holding_the_whole_input():
+    # n = the maximum, every |x| equal to a = 0.8f, which lies strictly inside
+    # its radix bins (0.8f = 0x3f4ccccd): with r = 0.01 n the level-0 bracket
+    # holds the whole input, with r = 1e-6 n the level-1 bracket does too; the
+    # exact threshold is a - r / n
+    n = B.GSSTV_NOALLOC_MAX_N
+    sign = np.where(np.random.default_rng(5).random(n) < 0.5, -1.0, 1.0)
+    a = float(np.float32(0.8))
+    x = (a * sign).astype(np.float32)
+    for r in (0.01 * n, 1e-6 * n):
+        _check(x, r)
+        _, _, tau_na, _ = _both(x, r)
+        assert tau_na == pytest.approx(a - r / n, rel=1e-12)
+    # values a few ulps apart: the bracket narrows through every level
+    k = np.random.default_rng(6).integers(0, 6, size=n)
+    y = (sign * a * (1.0 + k * 2.0**-23)).astype(np.float32)
+    for frac in (0.01, 1e-6):
+        _check(y, frac * n)
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum():
