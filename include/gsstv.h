@@ -83,7 +83,7 @@ typedef struct gsstv_handle gsstv_handle;
 /* Per-handle counters, for benchmarks and tests. */
 typedef struct gsstv_stats {
     int64_t iterations;        /* iterations run since create / reset_stats  */
-    int64_t tau_window_hits;   /* l1 thresholds found by the windowed search */
+    int64_t tau_window_hits;   /* l1 thresholds found by the fused pass's window */
     int64_t tau_exact_runs;    /* l1 thresholds found by the radix search    */
     double  k1_ms;             /* summed duration of the fused stencil kernel
                                   while timing is on (gsstv_set_timing)       */
@@ -91,6 +91,8 @@ typedef struct gsstv_stats {
     double  last_rel_change;   /* Eq. 28 ratio of the last iteration          */
     double  last_tau_s, last_tau_t; /* thresholds of the last iteration      */
     double  last_l2_scale;     /* min(1, eps / ||y4'/gamma_y4 - v||) (Eq. 23) */
+    int64_t tau_retry_hits;    /* l1 thresholds found by one retry pass over a
+                                  window placed after a miss                  */
 } gsstv_stats;
 
 /* Device views of the full state (float32, each a (N3,N1,N2) cube or a stack
@@ -210,6 +212,41 @@ int gsstv_batch_size(const gsstv_batch* b);
 int gsstv_batch_handle(gsstv_batch* b, int c, gsstv_handle** out);
 /* Releases the batch and every solver in it.  NULL is accepted. */
 int gsstv_batch_destroy(gsstv_batch* b);
+
+/* ---- one cube split into band slabs -------------------------------------
+ * Algorithm 1 on one cube whose bands are split into `nslabs` contiguous
+ * slabs (slab s owns bands [s N3 / nslabs, (s + 1) N3 / nslabs)), each stored
+ * in allocations of its own with one halo band on each side.  The only
+ * couplings between bands are D_s and D_s^T (Sec. II-A) and the global sums
+ * of a pass: the l2-ball norm of Eq. 23, the l1-ball thresholds (Sec. III-B)
+ * and the Eq. 28 norms.  So each pass runs every kernel once per slab, with
+ * the partial sums of all slabs finished together, and then refreshes the
+ * halos with one device copy per plane: u, q (y4), y1, y2 of the band above
+ * each slab and y2 of the band below.  The results equal those of a single
+ * handle up to the summation order of the global sums.  This is the data
+ * flow of a cube split over several GPUs (one slab per GPU, the partial sums
+ * all-reduced, the halo planes exchanged); here every slab lives on the
+ * current device.  Float32 storage only (GSSTV_ERR_ARG otherwise); 1 <=
+ * nslabs <= N3; each slab obeys gsstv_create's limits.
+ *
+ * The calls mirror the single-handle ones: views and cubes are whole-cube
+ * (N3, N1, N2) float32 device arrays owned by the caller; set_state fills
+ * the halos from the view; every call synchronises the stream before it
+ * returns, except load_observation.  gsstv_slabs_count returns the number of
+ * slabs and writes the bands each owns to bands_out (NULL allowed). */
+typedef struct gsstv_slabs gsstv_slabs;
+int gsstv_slabs_create(gsstv_slabs** out, int n1, int n2, int n3, int nslabs,
+                       const gsstv_params* p, void* stream);
+int gsstv_slabs_destroy(gsstv_slabs* s);
+int gsstv_slabs_load_observation(gsstv_slabs* s, const float* d_v);
+int gsstv_slabs_reset_state(gsstv_slabs* s);
+int gsstv_slabs_iterate(gsstv_slabs* s, int n, int* iters_done);
+int gsstv_slabs_solve(gsstv_slabs* s, const float* d_v, float* d_u, float* d_s,
+                      float* d_t, int* iters_done);
+int gsstv_slabs_get_state(gsstv_slabs* s, const gsstv_state_view* st);
+int gsstv_slabs_set_state(gsstv_slabs* s, const gsstv_state_view* st);
+int gsstv_slabs_get_stats(gsstv_slabs* s, gsstv_stats* out);
+int gsstv_slabs_count(const gsstv_slabs* s, int* bands_out);
 
 /* ---- reverse mode (gradients of the unrolled iteration) -------------------
  * The derivative of K passes of Algorithm 1 with respect to the observation

@@ -46,7 +46,7 @@ class GsstvStats(ctypes.Structure):
         ("iterations", c_int64), ("tau_window_hits", c_int64), ("tau_exact_runs", c_int64),
         ("k1_ms", c_double), ("k1_launches", c_int64),
         ("last_rel_change", c_double), ("last_tau_s", c_double), ("last_tau_t", c_double),
-        ("last_l2_scale", c_double),
+        ("last_l2_scale", c_double), ("tau_retry_hits", c_int64),
     ]
 
 
@@ -90,6 +90,17 @@ _SIGS = {
     "gsstv_vjp_step": (c_int, [c_void_p] + [ctypes.POINTER(GsstvStateView)] * 4 +
                        [c_void_p, ctypes.POINTER(c_double)]),
     "gsstv_unrolled_vjp": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
+    "gsstv_slabs_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int,
+                                   ctypes.POINTER(GsstvParams), c_void_p]),
+    "gsstv_slabs_destroy": (c_int, [c_void_p]),
+    "gsstv_slabs_load_observation": (c_int, [c_void_p, c_void_p]),
+    "gsstv_slabs_reset_state": (c_int, [c_void_p]),
+    "gsstv_slabs_iterate": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
+    "gsstv_slabs_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_int)]),
+    "gsstv_slabs_get_state": (c_int, [c_void_p, ctypes.POINTER(GsstvStateView)]),
+    "gsstv_slabs_set_state": (c_int, [c_void_p, ctypes.POINTER(GsstvStateView)]),
+    "gsstv_slabs_get_stats": (c_int, [c_void_p, ctypes.POINTER(GsstvStats)]),
+    "gsstv_slabs_count": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
     "gsstv_strerror": (ctypes.c_char_p, [c_int]),
 }
 
@@ -294,3 +305,58 @@ def gsstv_unrolled_vjp(h, iters: int, ckpt_every: int, d_ubar: int, d_vbar: int)
 
 def gsstv_strerror(code: int) -> str:
     return strerror(code)
+
+
+# ---- one cube split into band slabs -----------------------------------------
+def gsstv_slabs_create(n1: int, n2: int, n3: int, nslabs: int, params: GsstvParams, stream: int | None = None):
+    h = c_void_p()
+    _check(load().gsstv_slabs_create(ctypes.byref(h), n1, n2, n3, nslabs, ctypes.byref(params), stream or None),
+           "gsstv_slabs_create")
+    return h
+
+
+def gsstv_slabs_destroy(h):
+    _check(load().gsstv_slabs_destroy(h), "gsstv_slabs_destroy")
+
+
+def gsstv_slabs_load_observation(h, d_v: int):
+    _check(load().gsstv_slabs_load_observation(h, d_v), "gsstv_slabs_load_observation")
+
+
+def gsstv_slabs_reset_state(h):
+    _check(load().gsstv_slabs_reset_state(h), "gsstv_slabs_reset_state")
+
+
+def gsstv_slabs_iterate(h, n: int) -> int:
+    done = c_int(0)
+    _check(load().gsstv_slabs_iterate(h, n, ctypes.byref(done)), "gsstv_slabs_iterate")
+    return done.value
+
+
+def gsstv_slabs_solve(h, d_v: int, d_u: int, d_s: int | None = None, d_t: int | None = None) -> int:
+    done = c_int(0)
+    _check(load().gsstv_slabs_solve(h, d_v, d_u, d_s, d_t, ctypes.byref(done)), "gsstv_slabs_solve")
+    return done.value
+
+
+def gsstv_slabs_get_state(h, ptrs: dict):
+    v = _view(ptrs)
+    _check(load().gsstv_slabs_get_state(h, ctypes.byref(v)), "gsstv_slabs_get_state")
+
+
+def gsstv_slabs_set_state(h, ptrs: dict):
+    v = _view(ptrs)
+    _check(load().gsstv_slabs_set_state(h, ctypes.byref(v)), "gsstv_slabs_set_state")
+
+
+def gsstv_slabs_get_stats(h) -> GsstvStats:
+    s = GsstvStats()
+    _check(load().gsstv_slabs_get_stats(h, ctypes.byref(s)), "gsstv_slabs_get_stats")
+    return s
+
+
+def gsstv_slabs_count(h) -> list:
+    n = load().gsstv_slabs_count(h, None)
+    arr = (c_int * max(n, 1))()
+    load().gsstv_slabs_count(h, arr)
+    return list(arr[:n])

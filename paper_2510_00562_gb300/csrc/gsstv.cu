@@ -147,19 +147,20 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
         if (h->ev_used + 2 > (int)h->ev.size()) return GSSTV_ERR_INTERNAL;
         TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used], st)));
     }
+    const SlabPart whole = whole_cube(h->g);
     if (h->k1_variant == 1)
-        TRY(map_launch(launch_k1_tma(sto, h->g, h->maps[par], b, ip, h->sc, h->l1, h->k1_chunk, st)));
+        TRY(map_launch(launch_k1_tma(sto, h->g, h->maps[par], b, ip, h->sc, h->l1, h->k1_chunk, whole, st)));
     else
         TRY(map_launch(launch_k1(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, st)));
     if (timed) {
         TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used + 1], st)));
         h->ev_used += 2;
     }
-    TRY(map_launch(launch_window(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, st)));
+    TRY(map_launch(launch_window(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, whole, st)));
     for (int level = 0; level < 3; ++level)
-        TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, st)));
-    TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, st)));
-    TRY(map_launch(launch_k2(sto, h->g, b, ip, h->sc, h->k2_part, h->k2_cap, st)));
+        TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, whole, st)));
+    TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, whole, st)));
+    TRY(map_launch(launch_k2(sto, h->g, b, ip, h->sc, h->k2_part, h->k2_cap, whole, st)));
     return GSSTV_OK;
 }
 
@@ -317,8 +318,9 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.cand[1], kCandCap * sizeof(float));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.hcnt, 2 * kHistBins * sizeof(unsigned long long));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.hres, 2 * kHistBins * sizeof(unsigned long long));
-    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.k1_n, 2 * (size_t)h->k1_ctas * sizeof(unsigned long long));
-    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.k1_s, 2 * (size_t)h->k1_ctas * sizeof(double));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.k1_n, 4 * (size_t)h->k1_ctas * sizeof(unsigned long long));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.k1_s, 4 * (size_t)h->k1_ctas * sizeof(double));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.khist, 2 * (size_t)kK1Bins * sizeof(unsigned));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->k2_part, 3 * (size_t)h->k2_cap * sizeof(double));
     if (rc == GSSTV_OK) {
         h->ev.resize(512);
@@ -550,6 +552,7 @@ int gsstv_get_stats(gsstv_handle* h, gsstv_stats* out) {
     *out = h->stats;
     out->tau_window_hits = s.ctl[0].hits + s.ctl[1].hits;
     out->tau_exact_runs = s.ctl[0].exact_runs + s.ctl[1].exact_runs;
+    out->tau_retry_hits = s.ctl[0].retry_hits + s.ctl[1].retry_hits;
     return GSSTV_OK;
 }
 
@@ -559,7 +562,7 @@ int gsstv_reset_stats(gsstv_handle* h) {
     h->stats = gsstv_stats{};
     Scal s;
     TRY(read_scalars(h, &s));
-    for (int v = 0; v < 2; ++v) { s.ctl[v].hits = 0; s.ctl[v].exact_runs = 0; }
+    for (int v = 0; v < 2; ++v) { s.ctl[v].hits = 0; s.ctl[v].exact_runs = 0; s.ctl[v].retry_hits = 0; }
     return upload_scalars(h, s);
 }
 
@@ -868,6 +871,400 @@ int gsstv_batch_handle(gsstv_batch* b, int c, gsstv_handle** out) {
     if (!b || !out || c < 0 || c >= (int)b->h.size()) return GSSTV_ERR_ARG;
     *out = b->h[c];
     return GSSTV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one cube stored as band slabs
+// ---------------------------------------------------------------------------
+// The cube's bands are split into S contiguous slabs, each kept in allocations
+// of its own with one halo band on each side (only D_s and D_s^T couple
+// bands, Sec. II-A).  A pass runs every stage of the single-handle pass on
+// each slab in turn; the global sums of a stage (l1 window statistics,
+// histograms and candidates, radix histograms, the l2-ball and Eq. 28 norms)
+// go to one shared reduction area and are finished by the last CTA of all the
+// stage's launches.  After the pass the halos are refreshed with one copy per
+// plane: the band above a slab (u, q, y1, y2: what the next pass's u' of that
+// band needs) and the band below it (y2: D^T y2 there, for D_s^T).  This is
+// the data flow of a cube split over several GPUs, with the shared reduction
+// area standing in for all-reduces of the partial sums and the copies for the
+// halo exchange.
+struct gsstv_slabs {
+    int n1 = 0, n2 = 0, n3 = 0, S = 0;
+    gsstv_params p{};
+    cudaStream_t st = nullptr;
+    cudaStream_t cap = nullptr;
+    std::vector<gsstv_handle*> h;        // slab storage: bands [L0, L0 + h->g.n3) of the cube
+    std::vector<int> B0, B1, L0;         // owned bands [B0, B1), first stored band L0
+    std::vector<SlabPart> k1p, winp, radp, gatp, k2p;
+    std::vector<int> k1_chunk;
+    Scal* sc = nullptr;
+    L1Work l1{};
+    double* k2_part = nullptr;
+    int k2_cap = 0, win_cap = 0;
+    std::vector<void*> allocs;
+    int parity = 0;
+    cudaGraphExec_t gexec[2]{};
+    int graph_len = 0;
+    gsstv_stats stats{};
+};
+
+namespace {
+
+int slabs_alloc(gsstv_slabs* G, void** out, size_t bytes) {
+    *out = nullptr;
+    if (cudaMalloc(out, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return GSSTV_ERR_OOM;
+    }
+    G->allocs.push_back(*out);
+    return cuda_rc(cudaMemsetAsync(*out, 0, std::max<size_t>(bytes, 16), G->st));
+}
+
+void slabs_free(gsstv_slabs* G) {
+    for (int k = 0; k < 2; ++k)
+        if (G->gexec[k]) { cudaGraphExecDestroy(G->gexec[k]); G->gexec[k] = nullptr; }
+    if (G->st) cudaStreamSynchronize(G->st);
+    if (G->cap) { cudaStreamDestroy(G->cap); G->cap = nullptr; }
+    for (void* q : G->allocs) cudaFree(q);
+    G->allocs.clear();
+    for (gsstv_handle* x : G->h) gsstv_destroy(x);
+    G->h.clear();
+}
+
+// Numbers the CTAs of one stage across the slabs' launches.
+void number_stage(std::vector<SlabPart>& parts, const std::vector<int>& grids) {
+    int base = 0, total = 0;
+    for (int g : grids) total += g;
+    for (size_t s = 0; s < parts.size(); ++s) {
+        parts[s].cta_base = base;
+        parts[s].cta_total = total;
+        base += grids[s];
+    }
+}
+
+// One pass from parity `par` on `st`: every stage on every slab, then the halos.
+int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st) {
+    const int S = G->S;
+    const IterParams ip = iparams(G->h[0], par);
+    for (int s = 0; s < S; ++s) {
+        gsstv_handle* x = G->h[s];
+        TRY(map_launch(launch_k1_tma(GSSTV_FP32, x->g, x->maps[par], bufs(x, par), ip, G->sc, G->l1,
+                                     G->k1_chunk[s], G->k1p[s], st)));
+    }
+    for (int s = 0; s < S; ++s) {
+        gsstv_handle* x = G->h[s];
+        TRY(map_launch(launch_window(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->win_cap, G->winp[s], st)));
+    }
+    for (int level = 0; level < 3; ++level)
+        for (int s = 0; s < S; ++s) {
+            gsstv_handle* x = G->h[s];
+            TRY(map_launch(launch_fallback(GSSTV_FP32, level, x->g, bufs(x, par), ip, G->sc, G->l1, G->radp[s], st)));
+        }
+    for (int s = 0; s < S; ++s) {
+        gsstv_handle* x = G->h[s];
+        TRY(map_launch(launch_gather(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->gatp[s], st)));
+    }
+    for (int s = 0; s < S; ++s) {
+        gsstv_handle* x = G->h[s];
+        TRY(map_launch(launch_k2(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->k2_part, G->k2_cap, G->k2p[s], st)));
+    }
+    // halo exchange into the buffers the next pass reads (parity par ^ 1)
+    const int nx = par ^ 1;
+    for (int s = 0; s + 1 < S; ++s) {
+        gsstv_handle* lo = G->h[s];
+        gsstv_handle* hi = G->h[s + 1];
+        const size_t plane = (size_t)lo->g.n1 * lo->g.p2 * sizeof(float);
+        const size_t cube_lo = (size_t)lo->g.cube * sizeof(float), cube_hi = (size_t)hi->g.cube * sizeof(float);
+        // the band above slab s (its top halo) is slab s+1's first owned band
+        const size_t dst_top = (size_t)(G->B1[s] - G->L0[s]) * plane;
+        const size_t src_top = (size_t)(G->B1[s] - G->L0[s + 1]) * plane;
+        struct Pl { void* d; const void* s; int n; };
+        const Pl top[4] = {{lo->u[nx], hi->u[nx], 1}, {lo->q[nx], hi->q[nx], 1},
+                           {lo->y1[nx], hi->y1[nx], 2}, {lo->y2[nx], hi->y2[nx], 2}};
+        for (const Pl& q : top)
+            TRY(cuda_rc(cudaMemcpy2DAsync((char*)q.d + dst_top, cube_lo, (const char*)q.s + src_top, cube_hi, plane,
+                                          (size_t)q.n, cudaMemcpyDeviceToDevice, st)));
+        // the band below slab s+1 (its bottom halo) is slab s's last owned band
+        const size_t dst_bot = (size_t)(G->B1[s] - 1 - G->L0[s + 1]) * plane;
+        const size_t src_bot = (size_t)(G->B1[s] - 1 - G->L0[s]) * plane;
+        TRY(cuda_rc(cudaMemcpy2DAsync((char*)hi->y2[nx] + dst_bot, cube_hi, (const char*)lo->y2[nx] + src_bot, cube_lo,
+                                      plane, 2, cudaMemcpyDeviceToDevice, st)));
+    }
+    return GSSTV_OK;
+}
+
+int slabs_build_graph(gsstv_slabs* G, int par, int len) {
+    cudaGraph_t graph = nullptr;
+    TRY(cuda_rc(cudaStreamBeginCapture(G->cap, cudaStreamCaptureModeThreadLocal)));
+    int rc = GSSTV_OK;
+    int q = par;
+    for (int k = 0; k < len && rc == GSSTV_OK; ++k) {
+        rc = slabs_enqueue(G, q, G->cap);
+        q ^= 1;
+    }
+    cudaError_t e = cudaStreamEndCapture(G->cap, &graph);
+    if (rc != GSSTV_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return GSSTV_ERR_CUDA;
+    e = cudaGraphInstantiate(&G->gexec[par], graph, 0);
+    cudaGraphDestroy(graph);
+    return cuda_rc(e);
+}
+
+int slabs_run(gsstv_slabs* G, int n) {
+    const int Gl = G->p.graph_iters > 0 ? ((G->p.graph_iters + 1) / 2) * 2 : 0;
+    while (n > 0) {
+        if (Gl > 0 && n >= Gl) {
+            if (G->graph_len != Gl) {
+                for (int k = 0; k < 2; ++k)
+                    if (G->gexec[k]) { cudaGraphExecDestroy(G->gexec[k]); G->gexec[k] = nullptr; }
+            }
+            if (!G->gexec[G->parity]) TRY(slabs_build_graph(G, G->parity, Gl));
+            G->graph_len = Gl;
+            TRY(cuda_rc(cudaGraphLaunch(G->gexec[G->parity], G->st)));
+            n -= Gl;
+            G->stats.iterations += Gl;
+        } else {
+            TRY(slabs_enqueue(G, G->parity, G->st));
+            G->parity ^= 1;
+            --n;
+            G->stats.iterations += 1;
+        }
+    }
+    return GSSTV_OK;
+}
+
+int slabs_read_scalars(gsstv_slabs* G, Scal* out) {
+    TRY(cuda_rc(cudaMemcpyAsync(out, G->sc, sizeof(Scal), cudaMemcpyDeviceToHost, G->st)));
+    return cuda_rc(cudaStreamSynchronize(G->st));
+}
+
+int slabs_upload_scalars(gsstv_slabs* G) {
+    Scal s = initial_scalars(G->p);
+    TRY(cuda_rc(cudaMemcpyAsync(G->sc, &s, sizeof(Scal), cudaMemcpyHostToDevice, G->st)));
+    return cuda_rc(cudaStreamSynchronize(G->st));
+}
+
+// float32 copies between a whole-cube dense view (ncubes cubes of N floats)
+// and the stored bands [b0, b1) of one slab (pitched, its own cube stride)
+int slab_copy(gsstv_slabs* G, int s, const float* view, void* store, int ncubes, int b0, int b1, bool to_store,
+              const double* scale) {
+    gsstv_handle* x = G->h[s];
+    const long long N = (long long)G->n1 * G->n2 * G->n3;
+    const long long dense_off = (long long)b0 * G->n1 * G->n2;
+    const long long store_off = (long long)(b0 - G->L0[s]) * G->n1 * x->g.p2;
+    float* st_ = (float*)store + store_off;
+    if (to_store)
+        return map_launch(launch_copy_f32(view + dense_off, G->n2, N, st_, x->g.p2, x->g.cube, G->n1, G->n2,
+                                          b1 - b0, ncubes, nullptr, G->st));
+    return map_launch(launch_copy_f32(st_, x->g.p2, x->g.cube, const_cast<float*>(view) + dense_off, G->n2, N,
+                                      G->n1, G->n2, b1 - b0, ncubes, scale, G->st));
+}
+
+}  // namespace
+
+int gsstv_slabs_destroy(gsstv_slabs* G) {
+    if (!G) return GSSTV_OK;
+    slabs_free(G);
+    delete G;
+    return GSSTV_OK;
+}
+
+int gsstv_slabs_create(gsstv_slabs** out, int n1, int n2, int n3, int nslabs, const gsstv_params* p, void* stream) {
+    if (!out) return GSSTV_ERR_ARG;
+    *out = nullptr;
+    if (!shape_ok(n1, n2, n3) || nslabs < 1 || nslabs > n3) return GSSTV_ERR_ARG;
+    TRY(check_params(p));
+    if (p->storage != GSSTV_FP32) return GSSTV_ERR_ARG;
+    gsstv_slabs* G = new gsstv_slabs();
+    G->n1 = n1; G->n2 = n2; G->n3 = n3; G->S = nslabs;
+    G->p = *p;
+    G->st = (cudaStream_t)stream;
+    int rc = GSSTV_OK;
+    for (int s = 0; s < nslabs && rc == GSSTV_OK; ++s) {
+        const int b0 = (int)((long long)s * n3 / nslabs), b1 = (int)((long long)(s + 1) * n3 / nslabs);
+        const int l0 = std::max(b0 - 1, 0), l1 = std::min(b1 + 1, n3);
+        G->B0.push_back(b0); G->B1.push_back(b1); G->L0.push_back(l0);
+        gsstv_handle* x = nullptr;
+        rc = gsstv_create(&x, n1, n2, l1 - l0, p, stream);
+        if (rc == GSSTV_OK && x->k1_variant != 1) rc = GSSTV_ERR_ARG;    // the split runs the TMA-fed K1
+        if (x) G->h.push_back(x);
+        if (rc == GSSTV_OK) {
+            SlabPart sp;
+            sp.band0 = l0; sp.n3g = n3; sp.o0 = b0 - l0; sp.o1 = b1 - l0;
+            G->k1p.push_back(sp); G->winp.push_back(sp); G->radp.push_back(sp);
+            G->gatp.push_back(sp); G->k2p.push_back(sp);
+        }
+    }
+    if (rc == GSSTV_OK && cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        G->cap = nullptr;
+        rc = GSSTV_ERR_CUDA;
+    }
+    if (rc == GSSTV_OK) {
+        // each stage's launches, numbered across the slabs
+        std::vector<int> gk1, gw, gr, gg, gk2;
+        int max_chunk = 0;
+        for (int s = 0; s < nslabs; ++s) {
+            const Geom& g = G->h[s]->g;
+            const int c = k1_tma_part_chunk(g, G->k1p[s], 0);
+            G->k1_chunk.push_back(c);
+            max_chunk = std::max(max_chunk, c);
+            gk1.push_back(k1_tma_grid(g, G->k1p[s], c));
+            gw.push_back(window_grid(g, G->winp[s], 1 << 30));
+            gr.push_back(radix_grid(g, G->radp[s]));
+            gg.push_back(gather_grid(g, G->gatp[s]));
+            gk2.push_back(k2_grid(g, G->k2p[s], 1 << 30));
+        }
+        for (auto& sp : G->k1p) sp.max_chunk = max_chunk;
+        number_stage(G->k1p, gk1);
+        number_stage(G->winp, gw);
+        number_stage(G->radp, gr);
+        number_stage(G->gatp, gg);
+        number_stage(G->k2p, gk2);
+        const long long k1_total = G->k1p[0].cta_total, w_total = G->winp[0].cta_total;
+        G->win_cap = 1 << 30;
+        G->k2_cap = 1 << 30;
+        const size_t part_n = (size_t)std::max(4 * k1_total, 2 * w_total);
+        rc = slabs_alloc(G, (void**)&G->sc, sizeof(Scal));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.cand[0], kCandCap * sizeof(float));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.cand[1], kCandCap * sizeof(float));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.hcnt, 2 * kHistBins * sizeof(unsigned long long));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.hres, 2 * kHistBins * sizeof(unsigned long long));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.k1_n, part_n * sizeof(unsigned long long));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.k1_s, part_n * sizeof(double));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.khist, 2 * (size_t)kK1Bins * sizeof(unsigned));
+        if (rc == GSSTV_OK)
+            rc = slabs_alloc(G, (void**)&G->k2_part, 3 * (size_t)G->k2p[0].cta_total * sizeof(double));
+    }
+    if (rc == GSSTV_OK) rc = slabs_upload_scalars(G);
+    if (rc != GSSTV_OK) {
+        slabs_free(G);
+        delete G;
+        return rc;
+    }
+    *out = G;
+    return GSSTV_OK;
+}
+
+int gsstv_slabs_load_observation(gsstv_slabs* G, const float* d_v) {
+    if (!G || !d_v) return GSSTV_ERR_ARG;
+    for (int s = 0; s < G->S; ++s) {
+        gsstv_handle* x = G->h[s];
+        const Geom& g = x->g;
+        const float* src = d_v + (size_t)G->L0[s] * G->n1 * G->n2;
+        TRY(cuda_rc(cudaMemcpy2DAsync(x->v, (size_t)g.p2 * 4, src, (size_t)g.n2 * 4, (size_t)g.n2 * 4,
+                                      (size_t)g.n3 * g.n1, cudaMemcpyDeviceToDevice, G->st)));
+    }
+    return GSSTV_OK;
+}
+
+int gsstv_slabs_reset_state(gsstv_slabs* G) {
+    if (!G) return GSSTV_ERR_ARG;
+    TRY(cuda_rc(cudaStreamSynchronize(G->st)));
+    for (gsstv_handle* x : G->h) TRY(gsstv_reset_state(x));
+    G->parity = 0;
+    return slabs_upload_scalars(G);
+}
+
+int gsstv_slabs_iterate(gsstv_slabs* G, int n, int* iters_done) {
+    if (!G || n < 0) return GSSTV_ERR_ARG;
+    if (iters_done) *iters_done = 0;
+    int done = 0;
+    Scal s;
+    if (G->p.tol > 0.0) {
+        while (done < n) {
+            const int blk = std::min(G->p.check_every, n - done);
+            TRY(slabs_run(G, blk));
+            done += blk;
+            TRY(slabs_read_scalars(G, &s));
+            TRY(error_of(s));
+            G->stats.last_rel_change = s.u2 > 0 ? std::sqrt(s.du2 / s.u2) : INFINITY;
+            if (s.u2 > 0 && std::sqrt(s.du2 / s.u2) < G->p.tol) break;
+        }
+    } else {
+        TRY(slabs_run(G, n));
+        done = n;
+        TRY(slabs_read_scalars(G, &s));
+        TRY(error_of(s));
+        G->stats.last_rel_change = s.u2 > 0 ? std::sqrt(s.du2 / s.u2) : INFINITY;
+    }
+    for (gsstv_handle* x : G->h) x->parity = G->parity;
+    G->stats.last_tau_s = s.ctl[0].tau;
+    G->stats.last_tau_t = s.ctl[1].tau;
+    G->stats.last_l2_scale = s.c[G->parity];
+    G->stats.tau_window_hits = s.ctl[0].hits + s.ctl[1].hits;
+    G->stats.tau_exact_runs = s.ctl[0].exact_runs + s.ctl[1].exact_runs;
+    G->stats.tau_retry_hits = s.ctl[0].retry_hits + s.ctl[1].retry_hits;
+    if (iters_done) *iters_done = done;
+    return GSSTV_OK;
+}
+
+int gsstv_slabs_get_state(gsstv_slabs* G, const gsstv_state_view* v) {
+    if (!G || !view_ok(v)) return GSSTV_ERR_ARG;
+    const int par = G->parity;
+    for (int s = 0; s < G->S; ++s) {
+        gsstv_handle* x = G->h[s];
+        const int b0 = G->B0[s], b1 = G->B1[s];
+        TRY(slab_copy(G, s, v->u, x->u[par], 1, b0, b1, false, nullptr));
+        TRY(slab_copy(G, s, v->s, x->s[par], 1, b0, b1, false, nullptr));
+        TRY(slab_copy(G, s, v->t, x->t[par], 1, b0, b1, false, nullptr));
+        TRY(slab_copy(G, s, v->w1, x->w1[par], 6, b0, b1, false, nullptr));
+        TRY(slab_copy(G, s, v->w2, x->w2[par], 6, b0, b1, false, nullptr));
+        TRY(slab_copy(G, s, v->y1, x->y1[par], 2, b0, b1, false, nullptr));
+        TRY(slab_copy(G, s, v->y2, x->y2[par], 2, b0, b1, false, nullptr));
+        TRY(slab_copy(G, s, v->y3, x->y3[par], 1, b0, b1, false, nullptr));
+        TRY(slab_copy(G, s, v->y4, x->q[par], 1, b0, b1, false, &G->sc->c[par]));
+    }
+    return cuda_rc(cudaStreamSynchronize(G->st));
+}
+
+int gsstv_slabs_set_state(gsstv_slabs* G, const gsstv_state_view* v) {
+    if (!G || !view_ok(v)) return GSSTV_ERR_ARG;
+    const int par = G->parity;
+    for (int s = 0; s < G->S; ++s) {
+        gsstv_handle* x = G->h[s];
+        // the stored bands, halos included
+        const int b0 = G->L0[s], b1 = G->L0[s] + x->g.n3;
+        TRY(slab_copy(G, s, v->u, x->u[par], 1, b0, b1, true, nullptr));
+        TRY(slab_copy(G, s, v->s, x->s[par], 1, b0, b1, true, nullptr));
+        TRY(slab_copy(G, s, v->t, x->t[par], 1, b0, b1, true, nullptr));
+        TRY(slab_copy(G, s, v->w1, x->w1[par], 6, b0, b1, true, nullptr));
+        TRY(slab_copy(G, s, v->w2, x->w2[par], 6, b0, b1, true, nullptr));
+        TRY(slab_copy(G, s, v->y1, x->y1[par], 2, b0, b1, true, nullptr));
+        TRY(slab_copy(G, s, v->y2, x->y2[par], 2, b0, b1, true, nullptr));
+        TRY(slab_copy(G, s, v->y3, x->y3[par], 1, b0, b1, true, nullptr));
+        TRY(slab_copy(G, s, v->y4, x->q[par], 1, b0, b1, true, nullptr));
+    }
+    // y4 is now stored unscaled (c = 0); the threshold search starts afresh
+    return slabs_upload_scalars(G);
+}
+
+int gsstv_slabs_solve(gsstv_slabs* G, const float* d_v, float* d_u, float* d_s, float* d_t, int* iters_done) {
+    if (!G || !d_v || !d_u) return GSSTV_ERR_ARG;
+    TRY(gsstv_slabs_load_observation(G, d_v));
+    TRY(gsstv_slabs_reset_state(G));
+    TRY(gsstv_slabs_iterate(G, G->p.max_iter, iters_done));
+    const int par = G->parity;
+    for (int s = 0; s < G->S; ++s) {
+        gsstv_handle* x = G->h[s];
+        TRY(slab_copy(G, s, d_u, x->u[par], 1, G->B0[s], G->B1[s], false, nullptr));
+        if (d_s) TRY(slab_copy(G, s, d_s, x->s[par], 1, G->B0[s], G->B1[s], false, nullptr));
+        if (d_t) TRY(slab_copy(G, s, d_t, x->t[par], 1, G->B0[s], G->B1[s], false, nullptr));
+    }
+    return cuda_rc(cudaStreamSynchronize(G->st));
+}
+
+int gsstv_slabs_get_stats(gsstv_slabs* G, gsstv_stats* out) {
+    if (!G || !out) return GSSTV_ERR_ARG;
+    *out = G->stats;
+    return GSSTV_OK;
+}
+
+int gsstv_slabs_count(const gsstv_slabs* G, int* bands_out) {
+    if (!G) return 0;
+    if (bands_out)
+        for (int s = 0; s < G->S; ++s) bands_out[s] = G->B1[s] - G->B0[s];
+    return G->S;
 }
 
 const char* gsstv_strerror(int code) {

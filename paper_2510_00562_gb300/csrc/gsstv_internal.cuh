@@ -132,7 +132,11 @@ struct L1Ctl {
     unsigned long long n_above;// elements above the current bracket (exact)
     double s_above;            // their sum (exact up to double rounding)
     float g_lo, g_hi;          // gather window (g_lo, g_hi]
-    long long hits, exact_runs;
+    // K1 histogram of |x| for the next pass (after a miss): bins of the float
+    // key >> kHistShift, numbered from hbase; on while hist_left > 0
+    unsigned hbase;
+    int hist_left;
+    long long hits, exact_runs, retry_hits;
 };
 
 struct L1Acc {
@@ -159,6 +163,12 @@ constexpr unsigned kCandCap = 1u << 20; // candidate capacity per vector
 constexpr double kCandTarget = 65536.0;  // K1's window is sized for at most about this many candidates
 constexpr double kRetryTarget = 262144.0; // a retry window after a miss: at most about this many
 constexpr unsigned kGatherMax = 1u << 16; // a radix bracket this small is gathered, a larger one refined
+// K1's histogram of |x| near the predicted threshold: 1024 bins of 1/256
+// octave (the float key >> 15), four octaves, counted in packed 16-bit shared
+// counters (so a CTA may count at most 65535 voxels per vector)
+constexpr int kHistShift = 15;
+constexpr int kK1Bins = 1024;
+constexpr int kHistPasses = 6;           // passes the histogram stays on after a miss
 
 // Device workspace of the l1 machinery (shared layout with the standalone
 // projection entry point).
@@ -166,8 +176,9 @@ struct L1Work {
     float* cand[2];                    // kCandCap floats each
     unsigned long long* hcnt;          // [2][kHistBins]
     unsigned long long* hres;          // [2][kHistBins]
-    unsigned long long* k1_n;          // per K1 CTA: [2] counts
-    double* k1_s;                      // per K1 CTA: [2] sums
+    unsigned long long* k1_n;          // per K1 CTA: [4] counts (window s, t; histogram top s, t)
+    double* k1_s;                      // per K1 CTA: [4] sums
+    unsigned* khist;                   // [2][kK1Bins] K1 histogram counts (zero between passes)
 };
 
 // ---------------------------------------------------------------------------
@@ -290,28 +301,64 @@ struct K1Maps {
     CUtensorMap y1, y2, w1, w2, u, q, s, t, y3;
 };
 
+// The bands one launch updates when a cube is stored as band slabs in
+// separate allocations (only D_s couples bands, Sec. II-A, so a slab needs one
+// halo band on each side).  The launch's storage holds bands [band0, band0 +
+// g.n3) of a cube of n3g bands, and the launch updates the stored bands
+// [o0, o1).  Every global sum of a pass stage (the l2-ball norm, the Eq. 28
+// norms, the l1 threshold statistics) is finished by the last CTA of all the
+// stage's launches: this launch's CTAs are numbered from cta_base among
+// cta_total.  The whole cube in one launch: whole_cube(g).
+struct SlabPart {
+    int band0 = 0, n3g = 0, o0 = 0, o1 = 0;
+    int cta_base = 0, cta_total = 0;     // cta_total = 0: this launch alone
+    int max_chunk = 0;                   // K1: the longest band run of any launch of the stage
+};
+inline SlabPart whole_cube(const Geom& g) {
+    SlabPart s;
+    s.n3g = g.n3;
+    s.o1 = g.n3;
+    return s;
+}
+
 int k1_tma_ctas(const Geom& g);
 int k1_tma_chunk_candidates(const Geom& g, int* out, int cap);
 int k1_tma_configure(int storage);
 int k1_tma_maps(int storage, const Geom& g, const IterBufs& b, K1Maps* m);
+// CTAs of one K1 launch over the part's bands, and its bands per CTA (chunk
+// as for launch_k1_tma)
+int k1_tma_grid(const Geom& g, const SlabPart& sp, int chunk);
+int k1_tma_part_chunk(const Geom& g, const SlabPart& sp, int chunk);
 // chunk: bands per CTA (0 or out of range: the wave/prologue model's choice)
 int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p,
-                  Scal* sc, const L1Work& w, int chunk, cudaStream_t st);
+                  Scal* sc, const L1Work& w, int chunk, const SlabPart& sp, cudaStream_t st);
 
 int launch_k1(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
               const L1Work& w, int n_cta_slots, cudaStream_t st);
 int k1_grid_ctas(const Geom& g);
 int k1_configure(int storage);
 int light_configure(int storage);
+// CTAs of one launch of the threshold passes and of K2 over the part's bands
+int window_grid(const Geom& g, const SlabPart& sp, int part_cap);
+int radix_grid(const Geom& g, const SlabPart& sp);
+int gather_grid(const Geom& g, const SlabPart& sp);
+int k2_grid(const Geom& g, const SlabPart& sp, int part_cap);
 int launch_fallback(int storage, int level, const Geom& g, const IterBufs& b, const IterParams& p,
-                    Scal* sc, const L1Work& w, cudaStream_t st);
+                    Scal* sc, const L1Work& w, const SlabPart& sp, cudaStream_t st);
 int launch_gather(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
-                  const L1Work& w, cudaStream_t st);
+                  const L1Work& w, const SlabPart& sp, cudaStream_t st);
 int launch_window(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
-                  const L1Work& w, int part_cap, cudaStream_t st);
+                  const L1Work& w, int part_cap, const SlabPart& sp, cudaStream_t st);
 int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
-              double* part, int part_cap, cudaStream_t st);
+              double* part, int part_cap, const SlabPart& sp, cudaStream_t st);
 int k2_grid_ctas(const Geom& g);
+
+// float32 cubes between two layouts: ncubes cubes of nbands x n1 rows of n2
+// values, source and destination each with its own row pitch and cube stride
+// (in floats); y4 = (1 - *scale) q when scale is not NULL
+int launch_copy_f32(const float* src, long long src_pitch, long long src_cube, float* dst, long long dst_pitch,
+                    long long dst_cube, int n1, int n2, int nbands, int ncubes, const double* scale,
+                    cudaStream_t st);
 
 // state conversion (float32 views <-> pitched storage)
 int launch_pack(int storage, const float* src, void* dst, const Geom& g, int ncubes, cudaStream_t st);

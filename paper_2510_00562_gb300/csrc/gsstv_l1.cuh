@@ -115,15 +115,117 @@ static __device__ void l1_after_miss(L1Ctl& c, int rc, const WinInfo& wi, double
             b = ub;
         }
     }
-    c.prefix = 0; c.n_above = 0; c.s_above = 0.0; c.exact_runs++;
+    c.prefix = 0; c.n_above = 0; c.s_above = 0.0;
+    c.hist_left = kHistPasses;
     if (b > a && a >= 0.0) {
         c.need = NEED_WINDOW;
         c.g_lo = __double2float_rd(a);
         c.g_hi = __double2float_ru(b);
     } else {
         c.need = NEED_RADIX0;
+        c.exact_runs++;
     }
 }
+
+// Value of the lower edge of histogram bin b (b = kK1Bins: the top edge).
+__device__ __forceinline__ float hist_edge(unsigned hbase, int b) {
+    return __uint_as_float((hbase + (unsigned)b) << kHistShift);
+}
+// Is a histogram based at hbase made of finite, positive bin edges?
+__host__ __device__ __forceinline__ bool hist_base_ok(unsigned hbase) {
+    return hbase > 0u && ((unsigned long long)(hbase + kK1Bins) << kHistShift) < 0x7f800000ull;
+}
+
+// After K1's window missed: the bracket of the root that K1's histogram of
+// |x| gives.  hist: kK1Bins counts, bin b holding the |x| in [e_b, e_{b+1})
+// with e_b = hist_edge(hbase, b); n_top, s_top: count and sum of |x| >= e_top.
+// Taking every binned value at its bin's lower (upper) edge bounds phi at each
+// edge from below (above); the highest edge with phi >= 0 from below and the
+// lowest edge above it with phi < 0 from above bracket the root.  Returns 1
+// with the window (*lo, *hi] and the number of values inside it in *m, or 0
+// when the range does not bracket the root (or more than kCandCap values sit
+// in the bracket).  The bounds carry a relative margin, and the retry pass on
+// the window computes everything exactly, so a wrong bracket costs only time.
+// One whole block calls it; warp 0 works.
+static __device__ int l1_hist_bracket(const unsigned* hist, unsigned hbase, double n_top, double s_top,
+                                      double r, float* lo_out, float* hi_out, double* m_out, int* sh_i) {
+    constexpr int PER = kK1Bins / 32;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int b0 = lane * PER;
+        double c_l = 0.0, sl_l = 0.0, sh_l = 0.0;
+        for (int b = b0; b < b0 + PER; ++b) {
+            const double c = (double)__ldcg(hist + b);
+            c_l += c;
+            sl_l += c * (double)hist_edge(hbase, b);
+            sh_l += c * (double)hist_edge(hbase, b + 1);
+        }
+        // totals of the lanes above this one (exclusive suffix)
+        double c_in = c_l, sl_in = sl_l, sh_in = sh_l;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double c = __shfl_down_sync(0xffffffffu, c_in, o);
+            const double a = __shfl_down_sync(0xffffffffu, sl_in, o);
+            const double b = __shfl_down_sync(0xffffffffu, sh_in, o);
+            if (lane + o < 32) { c_in += c; sl_in += a; sh_in += b; }
+        }
+        const double total_sh = __shfl_sync(0xffffffffu, sh_in, 0);
+        // the float32-compensated sums carry about 1e-7 relative error
+        const double margin = 1e-6 * (s_top + total_sh + r);
+        const double top = (double)hist_edge(hbase, kK1Bins);
+        const double phi_top = s_top - n_top * top - r;         // exact up to the sums' rounding
+        // pass 1: the highest edge with phi >= margin from below
+        double N = n_top + (c_in - c_l), SL = s_top + (sl_in - sl_l);
+        int a_best = phi_top >= margin ? kK1Bins : -1;
+        for (int b = b0 + PER - 1; b >= b0 && a_best < 0; --b) {
+            const double e = (double)hist_edge(hbase, b);
+            const double c = (double)__ldcg(hist + b);
+            N += c;
+            SL += c * e;
+            if (SL - N * e - r >= margin) a_best = b;
+        }
+        int a_all = a_best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a_all = max(a_all, __shfl_xor_sync(0xffffffffu, a_all, o));
+        // pass 2: the lowest edge above it with phi < -margin from above
+        int c_best = kK1Bins + 1;
+        if (a_all >= 0 && a_all < kK1Bins) {
+            if (phi_top < -margin) c_best = kK1Bins;
+            N = n_top + (c_in - c_l);
+            double SH = s_top + (sh_in - sh_l);
+            for (int b = b0 + PER - 1; b >= b0; --b) {
+                const double e = (double)hist_edge(hbase, b);
+                const double c = (double)__ldcg(hist + b);
+                N += c;
+                SH += c * (double)hist_edge(hbase, b + 1);
+                if (b > a_all && SH - N * e - r < -margin) c_best = b;   // the lowest such b of this lane
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c_best = min(c_best, __shfl_xor_sync(0xffffffffu, c_best, o));
+        // values inside the bracket [e_a, e_c)
+        double m = 0.0;
+        if (a_all >= 0 && c_best <= kK1Bins)
+            for (int b = b0; b < b0 + PER; ++b)
+                if (b >= a_all && b < c_best) m += (double)__ldcg(hist + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        if (lane == 0) {
+            const bool ok = a_all >= 0 && a_all < kK1Bins && c_best <= kK1Bins && m <= (double)kCandCap;
+            sh_i[0] = ok ? 1 : 0;
+            if (ok) {
+                *lo_out = hist_edge(hbase, a_all);
+                *hi_out = hist_edge(hbase, c_best);
+                *m_out = m;
+            }
+        }
+    }
+    __syncthreads();
+    return sh_i[0];
+}
+
+
 
 // Records tau of this iteration and places the window of the next one around
 // the linear extrapolation of the last two thresholds.  After a window hit the
@@ -160,6 +262,9 @@ static __device__ void l1_record_tau(L1Ctl& c, double tau_new, double m_used, do
         hw = 2.0 * fabs(d1) + 1e-7 * tau_new;
     }
     if (c.dens > 0.0) hw = fmin(hw, 0.5 * kCandTarget / c.dens);
+    // the histogram of the next pass: four octaves from a quarter of the
+    // predicted threshold
+    c.hbase = center > 0.0 ? (__float_as_uint(__double2float_rd(0.25 * center)) >> kHistShift) : 0u;
     const double lo = fmax(center - hw, 0.0);
     const double hi = center + hw;
     c.theta_lo = __double2float_rd(lo);

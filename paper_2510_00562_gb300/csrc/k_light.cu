@@ -88,6 +88,7 @@ struct K2Args {
     IterParams p;
     Scal* sc;
     double* part;       // 3 doubles per CTA
+    SlabPart sp;        // the bands updated, and this launch's CTAs among the stage's
 };
 
 template <typename T>
@@ -102,13 +103,13 @@ __global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
     const unsigned it32 = (unsigned)a.sc->iter;       // seeds the 16-bit rounding streams
     const int quads = g.p2 / 4;
     const int strips = (g.n1 + K2_ROWS - 1) / K2_ROWS;
-    const long long items = (long long)g.n3 * strips * quads;
+    const long long items = (long long)(a.sp.o1 - a.sp.o0) * strips * quads;
     Kahan aq, adu, au;
     for (long long it = blockIdx.x * (long long)NT + threadIdx.x; it < items; it += (long long)gridDim.x * NT) {
         const int qd = (int)(it % quads);
         const long long rest = it / quads;
         const int strip = (int)(rest % strips);
-        const int b = (int)(rest / strips);
+        const int b = a.sp.o0 + (int)(rest / strips);
         const int j = qd * 4;
         const int i_s = strip * K2_ROWS;
         const int i_own = min(i_s + K2_ROWS, g.n1);            // own rows [i_s, i_own)
@@ -175,19 +176,21 @@ __global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
     const double q2 = block_sum(aq.value(), red_d);
     const double du2 = block_sum(adu.value(), red_d);
     const double u2 = block_sum(au.value(), red_d);
+    const int cta = a.sp.cta_base + blockIdx.x;
+    const int ncta = a.sp.cta_total > 0 ? a.sp.cta_total : (int)gridDim.x;
     if (threadIdx.x == 0) {
-        a.part[3 * blockIdx.x] = q2;
-        a.part[3 * blockIdx.x + 1] = du2;
-        a.part[3 * blockIdx.x + 2] = u2;
+        a.part[3 * cta] = q2;
+        a.part[3 * cta + 1] = du2;
+        a.part[3 * cta + 2] = u2;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->k2_ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->k2_ticket, 1u) == (unsigned)(ncta - 1));
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     double s0 = 0, s1 = 0, s2 = 0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += NT) {
+    for (int k = threadIdx.x; k < ncta; k += NT) {
         s0 += __ldcg(a.part + 3 * k);
         s1 += __ldcg(a.part + 3 * k + 1);
         s2 += __ldcg(a.part + 3 * k + 2);
@@ -222,6 +225,7 @@ struct CubeSrc {
     const Scal* sc;
     int parity;
     float gs, gt;
+    int o0, nb;         // the stored bands [o0, o0 + nb) this launch visits
     // Calls f(valid, |s~|, |t~|) for every voxel this thread owns, four
     // columns at a time in row order; every lane of a warp makes the same
     // number of calls (warp-collective work inside f is allowed).
@@ -230,12 +234,13 @@ struct CubeSrc {
         const float cs = (float)(1.0 - sc->c[parity]);
         const unsigned quads = (unsigned)g.p2 / 4u;
         const unsigned n1 = (unsigned)g.n1;
-        const unsigned total = (unsigned)g.n3 * n1 * quads;     // < 2^31 for any cube that fits
+        const unsigned total = (unsigned)nb * n1 * quads;       // < 2^31 for any cube that fits
+        const unsigned row0 = (unsigned)o0 * n1;
         for (unsigned base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
             const unsigned item = base + threadIdx.x;
             const bool live = item < total;
-            const unsigned row = live ? item / quads : 0u;       // b * n1 + i
-            const int j = (int)(item - row * quads) * 4;
+            const unsigned row = row0 + (live ? item / quads : 0u);   // b * n1 + i
+            const int j = (int)(item - (row - row0) * quads) * 4;
             const int i = (int)(row % n1);
             float4 s4 = make_float4(0, 0, 0, 0), t4 = s4, y34 = s4, yu4 = s4, q4 = s4;
             if (live) {
@@ -276,6 +281,8 @@ struct SearchArgs {
     Scal* sc;
     L1Work w;
     int nvec;        // 2 for the cube (s, t), 1 for a flat vector
+    int cta_base = 0, cta_total = 0;   // this launch's CTAs among the stage's (0: alone)
+    __device__ int total() const { return cta_total > 0 ? cta_total : (int)gridDim.x; }
 };
 
 // Radix histogram pass of one level for every vector that needs it; the last
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a,
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->fb_ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->fb_ticket, 1u) == (unsigned)(a.total() - 1));
     __syncthreads();
     if (!is_last) return;
     __threadfence();
@@ -413,7 +420,7 @@ __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a
     bc.flush(a.w.cand, a.sc);
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->g_ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->g_ticket, 1u) == (unsigned)(a.total() - 1));
     __syncthreads();
     if (!is_last) return;
     __threadfence();
@@ -475,13 +482,14 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
     bc.flush(a.w.cand, a.sc);
     const unsigned long long n0 = block_sum(w0.n, red_u), n1 = block_sum(w1.n, red_u);
     const double s0 = block_sum(w0.s.value(), red_d), s1 = block_sum(w1.s.value(), red_d);
+    const int cta = a.cta_base + blockIdx.x;
     if (threadIdx.x == 0) {
-        pn[2 * blockIdx.x] = n0; pn[2 * blockIdx.x + 1] = n1;
-        ps[2 * blockIdx.x] = s0; ps[2 * blockIdx.x + 1] = s1;
+        pn[2 * cta] = n0; pn[2 * cta + 1] = n1;
+        ps[2 * cta] = s0; ps[2 * cta + 1] = s1;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->w_ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->w_ticket, 1u) == (unsigned)(a.total() - 1));
     __syncthreads();
     if (!is_last) return;
     __threadfence();
@@ -490,7 +498,7 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
         L1Ctl& C = a.sc->ctl[v];
         unsigned long long n = 0;
         double sm = 0.0;
-        for (int k = threadIdx.x; k < (int)gridDim.x; k += NT) {
+        for (int k = threadIdx.x; k < a.total(); k += NT) {
             n += __ldcg(pn + 2 * k + v);
             sm += __ldcg(ps + 2 * k + v);
         }
@@ -503,8 +511,10 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
         if (threadIdx.x == 0) {
             if (rc == 0) {
                 l1_record_tau(C, tau, (double)min(m, kCandCap), hi - lo, false);
+                C.retry_hits++;
             } else {
                 C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0;
+                C.exact_runs++;
             }
             a.sc->acc[v].m = 0;
         }
@@ -596,9 +606,27 @@ int grid_for(long long n) {
     return (int)std::max(1ll, std::min(b, device_sms() * 16ll));
 }
 
+// voxels a part's launch visits
+long long part_voxels(const Geom& g, const SlabPart& sp) {
+    return (long long)(sp.o1 - sp.o0) * g.n1 * g.n2;
+}
+
+int k2_grid_part(const Geom& g, const SlabPart& sp) {
+    const long long items = (long long)(sp.o1 - sp.o0) * ((g.n1 + K2_ROWS - 1) / K2_ROWS) * (g.p2 / 4);
+    return grid_for(items);
+}
+
+int radix_grid_n(long long n) {
+    // enough CTAs that none sees more than 2^21 values (the shared bins are 32-bit)
+    const long long min_ctas = (n + (1ll << 21) - 1) >> 21;
+    return (int)std::max<long long>(std::min(grid_for(n), device_sms() * 3), min_ctas);
+}
+
+int gather_grid_n(long long n) { return std::min(grid_for(n), device_sms() * 4); }
+
 template <typename T>
 int launch_k2_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc, double* part,
-                int part_cap, cudaStream_t st) {
+                int part_cap, const SlabPart& sp, cudaStream_t st) {
     K2Args<T> a;
     a.g = g;
     a.u = (const T*)b.u; a.u_n = (const T*)b.u_n; a.s = (const T*)b.s; a.t = (const T*)b.t;
@@ -607,7 +635,8 @@ int launch_k2_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
     a.p = p;
     a.sc = sc;
     a.part = part;
-    const int ctas = std::min(k2_grid_ctas(g), part_cap);
+    a.sp = sp;
+    const int ctas = std::min(k2_grid_part(g, sp), part_cap);
     k2_light<T><<<ctas, NT, 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -615,15 +644,13 @@ int launch_k2_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
 template <typename Src>
 int launch_radix_src(const Src& src, long long n, const SearchArgs& a, int level, cudaStream_t st) {
     const size_t smem = 6 * kHistBins * sizeof(unsigned);
-    // enough CTAs that none sees more than 2^21 values (the shared bins are 32-bit)
-    const long long min_ctas = (n + (1ll << 21) - 1) >> 21;
-    const int grid = (int)std::max<long long>(std::min(grid_for(n), device_sms() * 3), min_ctas);
-    k_radix<Src><<<grid, NT, smem, st>>>(src, a, level);
+    k_radix<Src><<<radix_grid_n(n), NT, smem, st>>>(src, a, level);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 template <typename T>
-CubeSrc<T> make_cube_src(const Geom& g, const IterBufs& b, const IterParams& p, const Scal* sc) {
+CubeSrc<T> make_cube_src(const Geom& g, const IterBufs& b, const IterParams& p, const Scal* sc,
+                         const SlabPart& sp) {
     CubeSrc<T> c;
     c.g = g;
     c.s = (const T*)b.s; c.t = (const T*)b.t; c.y3 = (const T*)b.y3; c.q = (const T*)b.q;
@@ -631,35 +658,43 @@ CubeSrc<T> make_cube_src(const Geom& g, const IterBufs& b, const IterParams& p, 
     c.parity = p.parity;
     c.gs = p.gamma_s;
     c.gt = p.gamma_t;
+    c.o0 = sp.o0;
+    c.nb = sp.o1 - sp.o0;
     return c;
+}
+
+SearchArgs cube_args(Scal* sc, const L1Work& w, const SlabPart& sp) {
+    SearchArgs a{sc, w, 2};
+    a.cta_base = sp.cta_base;
+    a.cta_total = sp.cta_total;
+    return a;
 }
 
 template <typename T>
 int launch_fallback_t(int level, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
-                      const L1Work& w, cudaStream_t st) {
-    SearchArgs a{sc, w, 2};
-    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc);
-    return launch_radix_src(src, (long long)g.n3 * g.n1 * g.n2, a, level, st);
+                      const L1Work& w, const SlabPart& sp, cudaStream_t st) {
+    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc, sp);
+    return launch_radix_src(src, part_voxels(g, sp), cube_args(sc, w, sp), level, st);
 }
 
 template <typename T>
 int launch_gather_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc, const L1Work& w,
-                    cudaStream_t st) {
-    SearchArgs a{sc, w, 2};
-    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc);
-    const long long n = (long long)g.n3 * g.n1 * g.n2;
-    k_gather<CubeSrc<T>><<<std::min(grid_for(n), device_sms() * 4), NT, 0, st>>>(src, a);
+                    const SlabPart& sp, cudaStream_t st) {
+    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc, sp);
+    k_gather<CubeSrc<T>><<<gather_grid_n(part_voxels(g, sp)), NT, 0, st>>>(src, cube_args(sc, w, sp));
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int window_grid_n(long long n, int part_cap) {
+    return std::max(1, std::min({grid_for(n), device_sms() * 4, part_cap}));
 }
 
 template <typename T>
 int launch_window_t(const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc, const L1Work& w,
-                    int part_cap, cudaStream_t st) {
-    SearchArgs a{sc, w, 2};
-    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc);
-    const long long n = (long long)g.n3 * g.n1 * g.n2;
-    const int grid = std::max(1, std::min({grid_for(n), device_sms() * 4, part_cap}));
-    k_window<CubeSrc<T>><<<grid, NT, 0, st>>>(src, a, w.k1_n, w.k1_s);
+                    int part_cap, const SlabPart& sp, cudaStream_t st) {
+    const CubeSrc<T> src = make_cube_src<T>(g, b, p, sc, sp);
+    const int grid = window_grid_n(part_voxels(g, sp), part_cap);
+    k_window<CubeSrc<T>><<<grid, NT, 0, st>>>(src, cube_args(sc, w, sp), w.k1_n, w.k1_s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -722,50 +757,63 @@ int light_configure(int storage) {
     return e == cudaSuccess ? 0 : -3;
 }
 
-int k2_grid_ctas(const Geom& g) {
-    const long long items = (long long)g.n3 * ((g.n1 + K2_ROWS - 1) / K2_ROWS) * (g.p2 / 4);
-    return grid_for(items);
+int k2_grid_ctas(const Geom& g) { return k2_grid_part(g, whole_cube(g)); }
+
+int window_grid(const Geom& g, const SlabPart& sp, int part_cap) {
+    return window_grid_n(part_voxels(g, sp), part_cap);
 }
+int radix_grid(const Geom& g, const SlabPart& sp) { return radix_grid_n(part_voxels(g, sp)); }
+int gather_grid(const Geom& g, const SlabPart& sp) { return gather_grid_n(part_voxels(g, sp)); }
+int k2_grid(const Geom& g, const SlabPart& sp, int part_cap) { return std::min(k2_grid_part(g, sp), part_cap); }
 
 int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
-              double* part, int part_cap, cudaStream_t st) {
+              double* part, int part_cap, const SlabPart& sp, cudaStream_t st) {
     switch (storage) {
-        case 0: return launch_k2_t<float>(g, b, p, sc, part, part_cap, st);
-        case 1: return launch_k2_t<__nv_bfloat16>(g, b, p, sc, part, part_cap, st);
-        case 2: return launch_k2_t<__half>(g, b, p, sc, part, part_cap, st);
+        case 0: return launch_k2_t<float>(g, b, p, sc, part, part_cap, sp, st);
+        case 1: return launch_k2_t<__nv_bfloat16>(g, b, p, sc, part, part_cap, sp, st);
+        case 2: return launch_k2_t<__half>(g, b, p, sc, part, part_cap, sp, st);
     }
     return -1;
 }
 
 
 int launch_fallback(int storage, int level, const Geom& g, const IterBufs& b, const IterParams& p,
-                    Scal* sc, const L1Work& w, cudaStream_t st) {
+                    Scal* sc, const L1Work& w, const SlabPart& sp, cudaStream_t st) {
     switch (storage) {
-        case 0: return launch_fallback_t<float>(level, g, b, p, sc, w, st);
-        case 1: return launch_fallback_t<__nv_bfloat16>(level, g, b, p, sc, w, st);
-        case 2: return launch_fallback_t<__half>(level, g, b, p, sc, w, st);
+        case 0: return launch_fallback_t<float>(level, g, b, p, sc, w, sp, st);
+        case 1: return launch_fallback_t<__nv_bfloat16>(level, g, b, p, sc, w, sp, st);
+        case 2: return launch_fallback_t<__half>(level, g, b, p, sc, w, sp, st);
     }
     return -1;
 }
 
 int launch_gather(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
-                  const L1Work& w, cudaStream_t st) {
+                  const L1Work& w, const SlabPart& sp, cudaStream_t st) {
     switch (storage) {
-        case 0: return launch_gather_t<float>(g, b, p, sc, w, st);
-        case 1: return launch_gather_t<__nv_bfloat16>(g, b, p, sc, w, st);
-        case 2: return launch_gather_t<__half>(g, b, p, sc, w, st);
+        case 0: return launch_gather_t<float>(g, b, p, sc, w, sp, st);
+        case 1: return launch_gather_t<__nv_bfloat16>(g, b, p, sc, w, sp, st);
+        case 2: return launch_gather_t<__half>(g, b, p, sc, w, sp, st);
     }
     return -1;
 }
 
 int launch_window(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
-                  const L1Work& w, int part_cap, cudaStream_t st) {
+                  const L1Work& w, int part_cap, const SlabPart& sp, cudaStream_t st) {
     switch (storage) {
-        case 0: return launch_window_t<float>(g, b, p, sc, w, part_cap, st);
-        case 1: return launch_window_t<__nv_bfloat16>(g, b, p, sc, w, part_cap, st);
-        case 2: return launch_window_t<__half>(g, b, p, sc, w, part_cap, st);
+        case 0: return launch_window_t<float>(g, b, p, sc, w, part_cap, sp, st);
+        case 1: return launch_window_t<__nv_bfloat16>(g, b, p, sc, w, part_cap, sp, st);
+        case 2: return launch_window_t<__half>(g, b, p, sc, w, part_cap, sp, st);
     }
     return -1;
+}
+
+int launch_copy_f32(const float* src, long long src_pitch, long long src_cube, float* dst, long long dst_pitch,
+                    long long dst_cube, int n1, int n2, int nbands, int ncubes, const double* scale,
+                    cudaStream_t st) {
+    if (nbands <= 0 || ncubes <= 0) return 0;
+    Geom g{};
+    g.n1 = n1; g.n2 = n2; g.n3 = nbands;
+    return launch_convert(src, src_pitch, src_cube, dst, dst_pitch, dst_cube, g, ncubes, scale, st);
 }
 
 // dense float32 (ncubes, n3, n1, n2)  ->  pitched storage cubes
@@ -871,7 +919,7 @@ int l1_project_standalone(const float* x, long long n, double radius, float* out
         const SearchArgs a{sc, w, 1};
         for (int level = 0; level < 3 && rc == 0; ++level) rc = launch_radix_src(src, n, a, level, st);
         if (rc == 0) {
-            k_gather<FlatSrc><<<std::min(grid_for(n), device_sms() * 4), NT, 0, st>>>(src, a);
+            k_gather<FlatSrc><<<gather_grid_n(n), NT, 0, st>>>(src, a);
             k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
             if (cudaGetLastError() != cudaSuccess) rc = -3;
         }
@@ -969,7 +1017,7 @@ int l1_project_noalloc(const float* x, long long n, double radius, float* out, d
     const SearchArgs a{sc, w, 1};
     for (int level = 0; level < 3; ++level)
         if (launch_radix_src(src, n, a, level, st) != 0) return -3;
-    k_gather<FlatSrc><<<std::min(grid_for(n), device_sms() * 4), NT, 0, st>>>(src, a);
+    k_gather<FlatSrc><<<gather_grid_n(n), NT, 0, st>>>(src, a);
     k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
     if (cudaGetLastError() != cudaSuccess) return -3;
     double t = 0.0;

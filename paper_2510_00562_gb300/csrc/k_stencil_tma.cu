@@ -96,7 +96,8 @@ struct Lay {
     static constexpr int OFF_UP = OFF_WG + NWS * WG_B;
     static constexpr int OFF_G = OFF_UP + UP_B;
     static constexpr int OFF_CB = OFF_G + G_B;
-    static constexpr int OFF_BAR = OFF_CB + 2 * CB * 4;
+    static constexpr int OFF_HIST = OFF_CB + 2 * CB * 4;      // K1 histogram: 2 x kK1Bins packed 16-bit counts
+    static constexpr int OFF_BAR = OFF_HIST + kK1Bins * 4;
     static constexpr int SMEM = OFF_BAR + (NYS + NWS) * 8;
     // float offsets inside a y-group slot, and between planes
     static constexpr int YPL = Y_B / 4, WPL = W_B / 4;
@@ -119,12 +120,17 @@ struct K1TArgs {
     Scal* sc;
     L1Work l1;
     int chunk;
+    SlabPart sp;
+    int hist_fits;      // every CTA of the stage counts at most 65535 voxels
 };
 
-// Window of the l1 threshold search for this launch (see gsstv_l1.cuh).
+// Window of the l1 threshold search for this launch (see gsstv_l1.cuh), and
+// the histograms of |s~|, |t~| near the predicted thresholds when they are on.
 struct K1Win {
     bool s, t;
     float lo_s, hi_s, lo_t, hi_t;
+    bool hs, ht;
+    unsigned hb_s, hb_t;
 };
 
 // A thread's window statistics: count (a CTA covers at most a few thousand
@@ -137,6 +143,7 @@ struct K1Acc {
 // Per-CTA running state shared by the two tile paths.
 struct K1State {
     K1Acc acc_s, acc_t;
+    K1Acc top_s, top_t;          // |x| above the histogram's range
     unsigned n_y = 0, n_w = 0;   // groups issued so far (thread 0 only)
 };
 
@@ -201,6 +208,17 @@ __device__ __forceinline__ void win_add(K1Acc& A, bool take, float x) {
     A.s.c = take ? k.c : A.s.c;
 }
 
+// Counts x into the CTA's histogram (bins of the float key >> kHistShift from
+// hb; two 16-bit counters per shared word), or into the above-range
+// accumulator; values below the range are not needed.
+__device__ __forceinline__ void hist_add(bool on, float x, unsigned hb, unsigned* h, K1Acc& top) {
+    const unsigned kb = __float_as_uint(x) >> kHistShift;
+    const unsigned bin = kb - hb;                    // below the range wraps to a large value
+    const bool in = on && bin < (unsigned)kK1Bins;
+    if (in) atomicAdd(h + (bin >> 1), (bin & 1u) ? 65536u : 1u);
+    win_add(top, on && !in && kb >= hb + (unsigned)kK1Bins, x);
+}
+
 // value of a set selector: an int, or a std::integral_constant
 template <typename X> __device__ __forceinline__ constexpr int set_of(X x) {
     if constexpr (std::is_integral<X>::value) return x;
@@ -237,6 +255,7 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     float* up = reinterpret_cast<float*>(sm + L::OFF_UP);
     float* gs = reinterpret_cast<float*>(sm + L::OFF_G);
     float* cbuf = reinterpret_cast<float*>(sm + L::OFF_CB);
+    unsigned* hsm = reinterpret_cast<unsigned*>(sm + L::OFF_HIST);
     const int bstart = max(b0 - 1, 0);
     const int blast = min(b1, g.n3 - 1);
 
@@ -308,10 +327,12 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
             d1 = d.x;
             gcur = d.y;
         }
+        // D_s^T at the band's place in the whole cube (Neumann at its ends)
         const float gprev = gs[kc];
+        const int gb = bb + a.sp.band0;
         float dst_ = 0.f;
-        if (bb >= 1) dst_ += gprev;
-        if (bb <= g.n3 - 2) dst_ -= gcur;
+        if (gb >= 1) dst_ += gprev;
+        if (gb <= a.sp.n3g - 2) dst_ -= gcur;
         const int ku = r * SW + (c + OX);
         const float y4 = cs * ys[L::O_Q + ku];
         const float u = ys[L::O_U + ku];
@@ -487,6 +508,10 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
             append_shared(cs_, x_s, cbuf, ccnt, a.l1.cand[0], &a.sc->acc[0].m);
             append_shared(ct_, x_t, cbuf + L::CB, ccnt + 1, a.l1.cand[1], &a.sc->acc[1].m);
         }
+        if (W.hs || W.ht) {                               // the same for every thread
+            hist_add(W.hs && valid_t, x_s, W.hb_s, hsm, S.top_s);
+            hist_add(W.ht && valid_t, x_t, W.hb_t, hsm + kK1Bins / 2, S.top_t);
+        }
     };
 
     // ---- prologue: D^T y2 of band b0-1 and u' of band b0 ----
@@ -566,12 +591,12 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     __shared__ double red_d[64];
     __shared__ unsigned long long red_u[64];
     __shared__ unsigned ccnt[2], cbase[2];
-    __shared__ int is_last;
+    __shared__ int is_last, sh_flag;
     const Geom& g = a.g;
     const IterParams& P = a.p;
     const int i0 = blockIdx.y * L::TY, j0 = blockIdx.x * L::TX;
-    const int b0 = blockIdx.z * a.chunk;
-    const int b1 = min(g.n3, b0 + a.chunk);
+    const int b0 = a.sp.o0 + blockIdx.z * a.chunk;
+    const int b1 = min(a.sp.o1, b0 + a.chunk);
     const int tid = threadIdx.x;
     const float cs = (float)(1.0 - a.sc->c[P.parity]);
     K1Win W;
@@ -579,12 +604,23 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     W.t = !P.tau_exact && a.sc->radius[1] > 0.0 && a.sc->ctl[1].window_ok;
     W.lo_s = W.s ? a.sc->ctl[0].theta_lo : INFINITY; W.hi_s = W.s ? a.sc->ctl[0].theta_hi : INFINITY;
     W.lo_t = W.t ? a.sc->ctl[1].theta_lo : INFINITY; W.hi_t = W.t ? a.sc->ctl[1].theta_hi : INFINITY;
+    // the histograms: on after a recent miss, while a CTA's voxels fit the
+    // 16-bit counters
+    const bool hist_fits = a.hist_fits != 0;
+    W.hb_s = a.sc->ctl[0].hbase;
+    W.hb_t = a.sc->ctl[1].hbase;
+    W.hs = W.s && hist_fits && a.sc->ctl[0].hist_left > 0 && hist_base_ok(W.hb_s);
+    W.ht = W.t && hist_fits && a.sc->ctl[1].hist_left > 0 && hist_base_ok(W.hb_t);
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::OFF_BAR);
     if (tid == 0) {
         for (int k = 0; k < L::NYS + L::NWS; ++k) mbar_init(bars + k, 1);
         mbar_fence_init();
         ccnt[0] = ccnt[1] = 0;
+    }
+    if (W.hs || W.ht) {
+        unsigned* hsm = reinterpret_cast<unsigned*>(sm + L::OFF_HIST);
+        for (int k = tid; k < kK1Bins; k += L::NT) hsm[k] = 0u;
     }
     __syncthreads();
 
@@ -607,8 +643,9 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
         __syncthreads();
     }
 
-    const int cta = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const int ncta = gridDim.x * gridDim.y * gridDim.z;
+    // this CTA among every CTA of the pass stage (all slabs of a split cube)
+    const int cta = a.sp.cta_base + blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int ncta = a.sp.cta_total > 0 ? a.sp.cta_total : (int)(gridDim.x * gridDim.y * gridDim.z);
     if (W.s || W.t) {
         // the buffered window candidates join the global list (one atomic per vector)
         __syncthreads();
@@ -629,10 +666,31 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
         const unsigned long long nt = block_sum((unsigned long long)S.acc_t.n, red_u);
         const double st = block_sum_pair(S.acc_t.s, pbuf);
         if (tid == 0) {
-            a.l1.k1_n[2 * cta] = ns;
-            a.l1.k1_n[2 * cta + 1] = nt;
-            a.l1.k1_s[2 * cta] = ss;
-            a.l1.k1_s[2 * cta + 1] = st;
+            a.l1.k1_n[4 * cta] = ns;
+            a.l1.k1_n[4 * cta + 1] = nt;
+            a.l1.k1_s[4 * cta] = ss;
+            a.l1.k1_s[4 * cta + 1] = st;
+        }
+        if (W.hs || W.ht) {
+            // the histogram joins the global one (unpacked, nonzero bins only)
+            const unsigned* hsm = reinterpret_cast<const unsigned*>(sm + L::OFF_HIST);
+            for (int k = tid; k < kK1Bins; k += L::NT) {
+                const unsigned w = hsm[k];
+                const int v = k / (kK1Bins / 2), b = 2 * (k - v * (kK1Bins / 2));
+                unsigned* gh = a.l1.khist + v * kK1Bins + b;
+                if (w & 0xffffu) atomicAdd(gh, w & 0xffffu);
+                if (w >> 16) atomicAdd(gh + 1, w >> 16);
+            }
+            const unsigned long long hn_s = block_sum((unsigned long long)S.top_s.n, red_u);
+            const double hs_s = block_sum_pair(S.top_s.s, pbuf);
+            const unsigned long long hn_t = block_sum((unsigned long long)S.top_t.n, red_u);
+            const double hs_t = block_sum_pair(S.top_t.s, pbuf);
+            if (tid == 0) {
+                a.l1.k1_n[4 * cta + 2] = hn_s;
+                a.l1.k1_n[4 * cta + 3] = hn_t;
+                a.l1.k1_s[4 * cta + 2] = hs_s;
+                a.l1.k1_s[4 * cta + 3] = hs_t;
+            }
         }
     }
     __threadfence();
@@ -663,8 +721,8 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
         unsigned long long n = 0;
         double s = 0.0;
         for (int k = tid; k < ncta; k += L::NT) {
-            n += __ldcg(a.l1.k1_n + 2 * k + v);
-            s += __ldcg(a.l1.k1_s + 2 * k + v);
+            n += __ldcg(a.l1.k1_n + 4 * k + v);
+            s += __ldcg(a.l1.k1_s + 4 * k + v);
         }
         n = block_sum(n, red_u);
         s = block_sum(s, red_d);
@@ -674,11 +732,40 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
         WinInfo wi;
         // the tile's shared memory (up to the mbarriers) is idle now: stage the candidates there
         const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi,
-                                          reinterpret_cast<float*>(sm), L::OFF_BAR / 4);
+                                          reinterpret_cast<float*>(sm), L::OFF_HIST / 4);
+        // after a miss, the histogram (when on) brackets the root for one
+        // retry pass over the bracket
+        const bool hist_v = v == 0 ? W.hs : W.ht;
+        int hist_hit = 0;
+        float h_lo = 0.f, h_hi = 0.f;
+        double h_m = 0.0;
+        if (miss && hist_v) {
+            unsigned long long hn = 0;
+            double hs = 0.0;
+            for (int k = tid; k < ncta; k += L::NT) {
+                hn += __ldcg(a.l1.k1_n + 4 * k + 2 + v);
+                hs += __ldcg(a.l1.k1_s + 4 * k + 2 + v);
+            }
+            hn = block_sum(hn, red_u);
+            hs = block_sum(hs, red_d);
+            hist_hit = l1_hist_bracket(a.l1.khist + v * kK1Bins, v == 0 ? W.hb_s : W.hb_t, (double)hn, hs, r,
+                                       &h_lo, &h_hi, &h_m, &sh_flag);
+        }
+        if (hist_v) {
+            __syncthreads();
+            for (int k = tid; k < kK1Bins; k += L::NT) a.l1.khist[v * kK1Bins + k] = 0u;
+        }
         if (tid == 0) {
             if (!miss) {
                 l1_record_tau(C, tau, (double)min(m, kCandCap), thi - tlo, true);
                 C.hits++;
+                if (C.hist_left > 0) C.hist_left--;
+            } else if (hist_hit) {
+                C.prefix = 0; C.n_above = 0; C.s_above = 0.0;
+                C.need = NEED_WINDOW;
+                C.g_lo = h_lo;
+                C.g_hi = h_hi;
+                C.hist_left = kHistPasses;
             } else {
                 l1_after_miss(C, miss, wi, (double)n, m, tlo, thi);
             }
@@ -694,15 +781,15 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
 // prologue of about 1.5 band steps (its first copies, D^T y2 of the band
 // before, u' of its first band).  Picks the split of the bands (runs of at
 // least 8) that minimises idle fraction + prologue fraction.
-int tma_chunk(const Geom& g, int tiles) {
+int tma_chunk(int nb, int tiles) {
     const double kSms = (double)device_sms();
     constexpr double kPrologue = 1.5;
-    const int max_chunks = std::max(1, g.n3 / 8);
-    int best_len = g.n3;
+    const int max_chunks = std::max(1, nb / 8);
+    int best_len = nb;
     double best = 1e30;
     for (int chunks = 1; chunks <= max_chunks; ++chunks) {
-        const int len = (g.n3 + chunks - 1) / chunks;
-        const int used = (g.n3 + len - 1) / len;               // chunks actually launched
+        const int len = (nb + chunks - 1) / chunks;
+        const int used = (nb + len - 1) / len;                 // chunks actually launched
         const double units = (double)tiles * used;
         const double waves = std::ceil(units / kSms);
         const double waste = (waves - units / kSms) / waves + kPrologue / len;
@@ -740,7 +827,7 @@ int k1_tma_chunk_candidates(const Geom& g, int* out, int cap) {
         c.push_back({(waves - units / kSms) / waves + kPrologue / len, len});
     }
     std::stable_sort(c.begin(), c.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-    const int first = tma_chunk(g, tiles);
+    const int first = tma_chunk(g.n3, tiles);
     int n = 0;
     if (cap > 0) out[n++] = first;
     for (const auto& e : c)
@@ -773,9 +860,31 @@ int k1_tma_maps(int storage, const Geom& g, const IterBufs& b, K1Maps* m) {
     return rc ? -3 : 0;
 }
 
+namespace {
+// bands per CTA for the part's nb updated bands
+int part_chunk(const Geom& g, int nb, int chunk) {
+    const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
+    return chunk >= std::min(8, nb) && chunk <= nb ? chunk : tma_chunk(nb, tx * ty);
+}
+}  // namespace
+
+int k1_tma_part_chunk(const Geom& g, const SlabPart& sp, int chunk) {
+    return sp.o1 > sp.o0 ? part_chunk(g, sp.o1 - sp.o0, chunk) : 0;
+}
+
+int k1_tma_grid(const Geom& g, const SlabPart& sp, int chunk) {
+    const int nb = sp.o1 - sp.o0;
+    if (nb <= 0) return 0;
+    const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
+    const int c = part_chunk(g, nb, chunk);
+    return tx * ty * ((nb + c - 1) / c);
+}
+
 int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p,
-                  Scal* sc, const L1Work& w, int chunk, cudaStream_t st) {
+                  Scal* sc, const L1Work& w, int chunk, const SlabPart& sp, cudaStream_t st) {
     if (storage != 0) return -1;
+    const int nb = sp.o1 - sp.o0;
+    if (nb <= 0 || sp.o0 < 0 || sp.o1 > g.n3) return -1;
     K1TArgs a;
     a.g = g;
     a.u_n = (float*)b.u_n; a.w1_n = (float*)b.w1_n; a.w2_n = (float*)b.w2_n;
@@ -783,9 +892,14 @@ int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b
     a.p = p;
     a.sc = sc;
     a.l1 = w;
+    a.sp = sp;
     const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
-    a.chunk = chunk >= std::min(8, g.n3) && chunk <= g.n3 ? chunk : tma_chunk(g, tx * ty);
-    dim3 grid(tx, ty, (g.n3 + a.chunk - 1) / a.chunk);
+    a.chunk = part_chunk(g, nb, chunk);
+    // the histogram's packed 16-bit counters hold a CTA's voxels; a split cube
+    // passes the longest run of all its launches in sp.max_chunk, so that
+    // every launch of the stage agrees
+    a.hist_fits = std::max(a.chunk, sp.max_chunk) * Lay::NT <= 65535;
+    dim3 grid(tx, ty, (nb + a.chunk - 1) / a.chunk);
     k1_tma<<<grid, Lay::NT, Lay::SMEM, st>>>(m, a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -236,6 +236,77 @@ class GeoSSTVBatch:
         return {k: getattr(s, k) for k, _ in B.GsstvStats._fields_}
 
 
+class GeoSSTVSlabs:
+    """One N1 x N2 x N3 cube stored as `nslabs` band slabs (gsstv_slabs_*):
+    each slab in allocations of its own with one halo band on each side, the
+    global sums of every pass finished over all slabs, the halo planes copied
+    after every pass.  The same calls as GeoSSTVSolver for solves and states."""
+
+    def __init__(self, n1: int, n2: int, n3: int, nslabs: int, params: B.GsstvParams | None = None,
+                 stream: torch.cuda.Stream | None = None, **kw):
+        if not torch.cuda.is_available():
+            raise RuntimeError("GeoSSTVSlabs needs a CUDA device")
+        B.load()
+        self.shape = (n3, n1, n2)
+        self.params = params if params is not None else make_params(**kw)
+        self.stream = stream or torch.cuda.current_stream()
+        self.h = B.gsstv_slabs_create(n1, n2, n3, nslabs, self.params, self.stream.cuda_stream)
+        self.bands = B.gsstv_slabs_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            B.gsstv_slabs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _empty(self, lead=()):
+        return torch.empty(tuple(lead) + self.shape, dtype=torch.float32, device="cuda")
+
+    def solve(self, v: torch.Tensor):
+        """Runs max_iter passes from the standard start; returns (u, s, t, iters)."""
+        if tuple(v.shape) != self.shape or v.dtype != torch.float32 or not v.is_cuda or not v.is_contiguous():
+            raise ValueError("expected a contiguous float32 CUDA tensor of the cube shape")
+        u, s, t = self._empty(), self._empty(), self._empty()
+        n = B.gsstv_slabs_solve(self.h, v.data_ptr(), u.data_ptr(), s.data_ptr(), t.data_ptr())
+        return u, s, t, n
+
+    def load(self, v: torch.Tensor, reset: bool = True):
+        B.gsstv_slabs_load_observation(self.h, v.data_ptr())
+        if reset:
+            B.gsstv_slabs_reset_state(self.h)
+
+    def iterate(self, n: int) -> int:
+        return B.gsstv_slabs_iterate(self.h, n)
+
+    def get_state(self) -> dict:
+        st = {k: self._empty(STATE_LEAD[k]) for k in STATE_KEYS}
+        B.gsstv_slabs_get_state(self.h, {k: st[k].data_ptr() for k in STATE_KEYS})
+        return st
+
+    def set_state(self, st: dict):
+        for k in STATE_KEYS:
+            want = tuple(STATE_LEAD[k]) + self.shape
+            x = st[k]
+            if tuple(x.shape) != want or x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+                raise ValueError(f"state {k}: expected a contiguous float32 CUDA tensor of shape {want}")
+        B.gsstv_slabs_set_state(self.h, {k: st[k].data_ptr() for k in STATE_KEYS})
+
+    def stats(self) -> dict:
+        s = B.gsstv_slabs_get_stats(self.h)
+        return {k: getattr(s, k) for k, _ in B.GsstvStats._fields_}
+
+
 def project_l1ball(x: torch.Tensor, radius: float, out: torch.Tensor | None = None):
     """Projection of a float32 CUDA vector onto the l1 ball; returns (out, tau)."""
     if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
