@@ -101,10 +101,12 @@ def _global_l1(dist, x_local, r, n3, rank, world):
     return out, tau
 
 
-def slab_step(dist, st: o.State, v_local, p: o.Params, n3: int, rank: int, world: int) -> o.State:
+def slab_step(dist, st: o.State, v_local, p: o.Params, n3: int, rank: int, world: int,
+              v_whole=None) -> o.State:
     """One pass of Algorithm 1 on this rank's slab (see the module docstring).
 
-    st, v_local: the stored bands [L0, L1).  Returns the next local state,
+    st, v_local: the stored bands [L0, L1); v_whole (optional): the whole
+    observation, gathered here when not given.  Returns the next local state,
     with the halo bands refreshed from the neighbours."""
     v_local = np.asarray(v_local, dtype=np.float64)
     b0, b1, l0, l1 = slab_bands(rank, world, n3)
@@ -131,7 +133,8 @@ def slab_step(dist, st: o.State, v_local, p: o.Params, n3: int, rank: int, world
     y4p = st.y4 + p.gamma_y4 * a4
     # the l2-ball step on the whole vector: y4 = y4' - g P_B(y4' / g)
     z_whole = _gather_bands(dist, _owned(y4p / p.gamma_y4, rank, world, n3), n3, rank, world)
-    v_whole = _gather_bands(dist, _owned(v_local, rank, world, n3), n3, rank, world)
+    if v_whole is None:
+        v_whole = _gather_bands(dist, _owned(v_local, rank, world, n3), n3, rank, world)
     pz = o.proj_l2ball(z_whole, v_whole, p.eps)
     y41 = np.zeros_like(y4p)
     y41[b0 - l0:b1 - l0] = y4p[b0 - l0:b1 - l0] - p.gamma_y4 * pz[b0:b1]
@@ -155,5 +158,5 @@ def solve_slabs(dist, v, p: o.Params, iters: int, rank: int, world: int, state: 
     _, _, l0, l1 = slab_bands(rank, world, n3)
     v_local = v[l0:l1]
     for _ in range(iters):
-        st = slab_step(dist, st, v_local, p, n3, rank, world)
+        st = slab_step(dist, st, v_local, p, n3, rank, world, v_whole=v)
     return gather_state(dist, st, n3, rank, world)

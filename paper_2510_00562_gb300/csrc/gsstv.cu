@@ -1,11 +1,12 @@
 // Host driver and C ABI of libgsstv (declared in include/gsstv.h).
 //
-// One iteration of Algorithm 1 is seven launches on the handle's stream:
+// One iteration of Algorithm 1 is nine launches on the handle's stream:
 //   K1  fused stencil pass (u, w1, w2, y1, y2 and the l1 window statistics);
-//   W   one retry window for a threshold whose K1 window missed;
+//   W, F  one retry window for a threshold whose K1 window missed, and its
+//       finish (one CTA);
 //   R0, R1, R2  radix passes of the exact l1-threshold search (each returns at
 //       once unless the previous step left that level pending);
-//   G   gather of the bracket bin (same early return);
+//   G, F  gather of the bracket bin and its finish (same early return);
 //   K2  light pass (s, t, y3, y4 and the l2-ball norm).
 // Every scalar that couples the iteration (the thresholds tau_s, tau_t and the
 // l2-ball scale c) stays on the device, so a block of iterations can be
@@ -157,9 +158,12 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
         h->ev_used += 2;
     }
     TRY(map_launch(launch_window(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, whole, st)));
+    TRY(map_launch(launch_search_finish(0, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
+                                        window_grid(h->g, whole, h->k1_ctas), st)));
     for (int level = 0; level < 3; ++level)
         TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, whole, st)));
     TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, whole, st)));
+    TRY(map_launch(launch_search_finish(1, h->sc, h->l1, 2, nullptr, nullptr, 0, st)));
     TRY(map_launch(launch_k2(sto, h->g, b, ip, h->sc, h->k2_part, h->k2_cap, whole, st)));
     return GSSTV_OK;
 }
@@ -956,6 +960,7 @@ int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st) {
         gsstv_handle* x = G->h[s];
         TRY(map_launch(launch_window(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->win_cap, G->winp[s], st)));
     }
+    TRY(map_launch(launch_search_finish(0, G->sc, G->l1, 2, G->l1.k1_n, G->l1.k1_s, G->winp[0].cta_total, st)));
     for (int level = 0; level < 3; ++level)
         for (int s = 0; s < S; ++s) {
             gsstv_handle* x = G->h[s];
@@ -965,6 +970,7 @@ int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st) {
         gsstv_handle* x = G->h[s];
         TRY(map_launch(launch_gather(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->gatp[s], st)));
     }
+    TRY(map_launch(launch_search_finish(1, G->sc, G->l1, 2, nullptr, nullptr, 0, st)));
     for (int s = 0; s < S; ++s) {
         gsstv_handle* x = G->h[s];
         TRY(map_launch(launch_k2(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->k2_part, G->k2_cap, G->k2p[s], st)));

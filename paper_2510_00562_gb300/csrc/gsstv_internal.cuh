@@ -165,9 +165,11 @@ constexpr double kRetryTarget = 262144.0; // a retry window after a miss: at mos
 constexpr unsigned kGatherMax = 1u << 16; // a radix bracket this small is gathered, a larger one refined
 // K1's histogram of |x| near the predicted threshold: 1024 bins of 1/256
 // octave (the float key >> 15), four octaves, counted in packed 16-bit shared
-// counters (so a CTA may count at most 65535 voxels per vector)
+// counters (so a CTA may count at most 65535 voxels per vector) from a 1/32
+// sample of the voxels
 constexpr int kHistShift = 15;
 constexpr int kK1Bins = 1024;
+constexpr int kHistSample = 32;
 constexpr int kHistPasses = 6;           // passes the histogram stays on after a miss
 
 // Device workspace of the l1 machinery (shared layout with the standalone
@@ -232,9 +234,62 @@ __device__ __forceinline__ float soft(float x, float tau) {
 // value of a non-negative float given by its bit pattern, and the size of
 // one unit of its last mantissa bit (as double, both exact)
 __device__ __forceinline__ double key_value(unsigned key) { return (double)__uint_as_float(key); }
+// 2^(e - 150) for the float's biased exponent e (2^-149 for subnormals),
+// built as the bit pattern of a double: biased exponent (e - 150) + 1023
 __device__ __forceinline__ double key_ulp(unsigned key) {
-    unsigned e = (key >> 23) & 0xffu;
-    return ldexp(1.0, (e == 0 ? 1 : (int)e) - 150);
+    const unsigned e = (key >> 23) & 0xffu;
+    return __longlong_as_double((long long)((e == 0u ? 1u : e) + 873u) << 52);
+}
+
+// Sums over the CTA carried as unevaluated float pairs (hi + lo, Knuth's
+// two-sum at every step): FP64 work on this part runs at a small fraction of
+// the FP32 rate, so a CTA-wide sum keeps it to thread 0.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float bhi, float blo) {
+    float s, e;
+    two_sum(hi, bhi, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, blo));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+// The CTA's sum of the threads' compensated sums; the result (a double) is
+// valid on thread 0 only.  buf: >= 32 float2 of shared memory.
+__device__ __forceinline__ double block_sum_pair(const Kahan& k, float2* buf) {
+    float hi = k.s, lo = -k.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
+        pair_add(hi, lo, bh, bl);
+    }
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) buf[w] = make_float2(hi, lo);
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        float h = buf[0].x, l = buf[0].y;
+        for (int k2 = 1; k2 < nw; ++k2) pair_add(h, l, buf[k2].x, buf[k2].y);
+        r = (double)h + (double)l;
+    }
+    return r;
+}
+// Integer sum over the CTA (32-bit lanes, 64-bit result), every thread gets it.
+__device__ __forceinline__ unsigned long long block_count(unsigned x, unsigned long long* buf) {
+    unsigned long long v = x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) buf[w] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+    for (int k = 0; k < nw; ++k) r += buf[k];
+    __syncthreads();
+    return r;
 }
 
 // s~ = s - g_s y4 and t~ = t - g_t (D_v^T y3 + y4) of one voxel (the inputs of
@@ -351,6 +406,11 @@ int launch_window(int storage, const Geom& g, const IterBufs& b, const IterParam
                   const L1Work& w, int part_cap, const SlabPart& sp, cudaStream_t st);
 int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
               double* part, int part_cap, const SlabPart& sp, cudaStream_t st);
+// The finish of the retry window (mode 0; parts: CTAs of the window pass(es),
+// their partial sums in pn / ps) or of the gathered radix bracket (mode 1),
+// for every vector that needs it: one launch after the pass(es) it finishes.
+int launch_search_finish(int mode, Scal* sc, const L1Work& w, int nvec, const unsigned long long* pn,
+                         const double* ps, int parts, cudaStream_t st);
 int k2_grid_ctas(const Geom& g);
 
 // float32 cubes between two layouts: ncubes cubes of nbands x n1 rows of n2

@@ -30,6 +30,199 @@ struct WinInfo {
     double n_lo = 0.0;     // count of |x| > theta_lo
 };
 
+// Calls f(x, k) for every candidate x = cand[k], k < m, with 16 values in
+// flight per thread (four 16-byte loads): one CTA walking a long candidate
+// list is bound by the latency of its loads, not by their bandwidth.  cand
+// must be 16-byte aligned (every candidate buffer starts on a 256-byte
+// boundary).
+template <typename F>
+__device__ __forceinline__ void for_each_candidate(const float* cand, unsigned m, F&& f) {
+    const unsigned nt = blockDim.x, m4 = m / 4u;
+    const float4* c4 = reinterpret_cast<const float4*>(cand);
+    unsigned k = threadIdx.x;
+    for (; k + 3u * nt < m4; k += 4u * nt) {
+        float4 q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[j] = __ldcg(c4 + k + j * nt);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned b = 4u * (k + j * nt);
+            f(q[j].x, b); f(q[j].y, b + 1u); f(q[j].z, b + 2u); f(q[j].w, b + 3u);
+        }
+    }
+    for (; k < m4; k += nt) {
+        const float4 q = __ldcg(c4 + k);
+        f(q.x, 4u * k); f(q.y, 4u * k + 1u); f(q.z, 4u * k + 2u); f(q.w, 4u * k + 3u);
+    }
+    for (unsigned j = 4u * m4 + threadIdx.x; j < m; j += nt) f(__ldcg(cand + j), j);
+}
+
+// Many candidates: before Michelot's step, narrow the window on the GPU's
+// float keys.  For x >= 0 the IEEE bit pattern is monotone in the value;
+// bins of 2^shift keys aligned to multiples of 2^shift (shift <= 20) never
+// straddle an exponent, so the sum of a bin's values is exact:
+//   count x (value of the bin's lowest key) + ulp x (sum of key residues).
+// One pass over the candidates fills at most kNarrowBins bins; phi at every
+// bin edge follows, and the bin whose lower edge is the highest with
+// phi >= 0 brackets the root; the bins above it join the "above" count and
+// sum.  Repeated on that bin until it holds at most kNarrowStage values,
+// which are then staged in the scratch for Michelot's step.
+constexpr int kNarrowBins = 2048;
+constexpr unsigned kNarrowStage = 3 * kNarrowBins;   // floats the scratch stages
+constexpr unsigned kNarrowMin = 4096;                // candidates beyond this are narrowed first
+
+// Whole block.  cand[0..m): the candidates, every one in (klo, khi] as keys;
+// scr: 3 kNarrowBins unsigned of shared memory; sh_d: 4 doubles, wtot: 64
+// unsigned long long of shared memory.  On
+// return 0: (klo, khi] narrowed, n_hi / s_hi now count everything above khi,
+// and the *m_st values in the new window are staged as floats in scr.
+// Returns 1 when phi at the window's lower end is negative (the root lies
+// below it; sh_d[2], sh_d[3]: phi there and the count above it), 2 when the
+// window is too wide to narrow (more than 16 binary orders) or does not
+// narrow in a few rounds.
+static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m, double& n_hi, double& s_hi,
+                                unsigned& klo, unsigned& khi, double r, unsigned* scr, unsigned* m_st, int* sh_i,
+                                double* sh_d, unsigned long long* wtot) {
+    // every candidate, from global memory (batched loads) or from shared memory
+    auto each = [&](auto&& f) {
+        if (cand_shared) {
+            for (unsigned k = threadIdx.x; k < m; k += blockDim.x) f(cand[k], k);
+        } else {
+            for_each_candidate(cand, m, f);
+        }
+    };
+    unsigned* cnt = scr;
+    unsigned* rlo = scr + kNarrowBins;
+    unsigned* rhi = scr + 2 * kNarrowBins;
+    for (int round = 0; round < 8; ++round) {
+        int shift = 0;
+        while (shift < 20 && ((khi >> shift) - (klo >> shift)) >= (unsigned)kNarrowBins) ++shift;
+        const unsigned base = klo >> shift;
+        const int nb = (int)((khi >> shift) - base) + 1;
+        // the integer sums below need a window of at most 16 binary orders
+        if (max((int)((khi >> 23) & 0xffu), 1) - max((int)(((klo + 1u) >> 23) & 0xffu), 1) > 16) return 2;
+        __syncthreads();
+        for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) scr[k] = 0u;
+        __syncthreads();
+        each([&](float x, unsigned) {
+            const unsigned key = __float_as_uint(x);
+            if (key > klo && key <= khi) {
+                const int b = (int)((key >> shift) - base);
+                const unsigned res = key - ((key >> shift) << shift);
+                atomicAdd(cnt + b, 1u);
+                if (res) {
+                    atomicAdd(rlo + b, res & 1023u);
+                    atomicAdd(rhi + b, res >> 10);
+                }
+            }
+        });
+        __syncthreads();
+        // Exact sums in units of u0, the ulp at the window's lowest key: every
+        // float in the window is an integer multiple of u0 (below 2^40 of
+        // them while the window spans at most 16 binary orders), so a bin's
+        // count and sum and their suffix sums are exact 64-bit integers; FP64
+        // appears only in the comparisons of phi with 0 at a few bin edges.
+        const unsigned k0 = klo + 1u;
+        const int e0 = max((int)((k0 >> 23) & 0xffu), 1);
+        const double u0 = key_ulp(k0);
+        auto V = [&](unsigned key) -> unsigned long long {       // value / u0 of a key in the window
+            const unsigned e = (key >> 23) & 0xffu;
+            const unsigned long long mant = (key & 0x7fffffu) | (e ? 0x800000u : 0u);
+            return mant << (max((int)e, 1) - e0);
+        };
+        auto bin_int = [&](int b) -> unsigned long long {        // sum of bin b, in units of u0
+            const unsigned lk = (base + (unsigned)b) << shift;
+            const unsigned long long res = (unsigned long long)rhi[b] * 1024ull + rlo[b];
+            return (unsigned long long)cnt[b] * V(lk) + (res << (max((int)((lk >> 23) & 0xffu), 1) - e0));
+        };
+        const int nt = (int)blockDim.x;
+        const int per = (nb + nt - 1) / nt;
+        const int c0 = (int)threadIdx.x * per, c1 = min(nb, c0 + per);
+        unsigned long long Nc = 0, Sc = 0;
+        for (int b = c0; b < c1; ++b) { Nc += cnt[b]; Sc += bin_int(b); }
+        // totals of the chunks above this thread's (exclusive suffix over threads)
+        unsigned long long Ni = Nc, Si = Sc;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (nt + 31) >> 5;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long a = __shfl_down_sync(0xffffffffu, Ni, o);
+            const unsigned long long c = __shfl_down_sync(0xffffffffu, Si, o);
+            if (lane + o < 32) { Ni += a; Si += c; }
+        }
+        if (lane == 0) { wtot[wid] = Ni; wtot[32 + wid] = Si; }
+        __syncthreads();
+        unsigned long long Nup = Ni - Nc, Sup = Si - Sc;          // chunks above, inside this warp
+        for (int w = wid + 1; w < nw; ++w) { Nup += wtot[w]; Sup += wtot[32 + w]; }
+        // phi at an edge with the bins from b up and everything above the window
+        auto phi_at = [&](double e, unsigned long long e_int, unsigned long long Nsuf, unsigned long long Ssuf) {
+            return s_hi - n_hi * e - r + (double)(long long)(Ssuf - Nsuf * e_int) * u0;
+        };
+        auto edge_phi = [&](int b, unsigned long long Nsuf, unsigned long long Ssuf) {
+            if (b == 0)       // the window's lower end (exclusive)
+                return s_hi + (double)Ssuf * u0 - (n_hi + (double)Nsuf) * (double)__uint_as_float(klo) - r;
+            const unsigned lk = (base + (unsigned)b) << shift;
+            return phi_at((double)__uint_as_float(lk), V(lk), Nsuf, Ssuf);
+        };
+        // the chunk whose lowest edge is the highest with phi >= 0
+        const bool has = c0 < c1;
+        const bool ok = has && edge_phi(c0, Nup + Nc, Sup + Sc) >= 0.0;
+        if (threadIdx.x == 0) sh_i[0] = -1;
+        __syncthreads();
+        if (ok) atomicMax(sh_i, (int)threadIdx.x);
+        __syncthreads();
+        const int owner = sh_i[0];
+        __syncthreads();
+        if (owner < 0) {
+            if (threadIdx.x == 0) {
+                sh_i[0] = -1;
+                // phi at the window's lower end, and the count above it
+                sh_d[2] = edge_phi(0, Nup + Nc, Sup + Sc);
+                sh_d[3] = n_hi + (double)(Nup + Nc);
+            }
+        } else if ((int)threadIdx.x == owner) {
+            // this chunk: its highest bin whose lower edge has phi >= 0
+            unsigned long long N = Nup, S = Sup;
+            int best = c0;
+            unsigned long long bn = Nup, bs = Sup;
+            for (int b = c1 - 1; b >= c0; --b) {
+                const unsigned long long na = N, sa = S;         // bins above b
+                N += cnt[b];
+                S += bin_int(b);
+                if (edge_phi(b, N, S) >= 0.0) { best = b; bn = na; bs = sa; break; }
+            }
+            sh_i[0] = best;
+            sh_d[0] = n_hi + (double)bn;
+            sh_d[1] = s_hi + (double)bs * u0;
+        }
+        __syncthreads();
+        const int kb = sh_i[0];
+        if (kb < 0) { __syncthreads(); return 1; }
+        const unsigned count = cnt[kb];
+        n_hi = sh_d[0];
+        s_hi = sh_d[1];
+        const unsigned nlo = kb == 0 ? klo : ((base + (unsigned)kb) << shift) - 1u;
+        const unsigned nhi = min(khi, ((base + (unsigned)kb + 1u) << shift) - 1u);
+        klo = nlo;
+        khi = nhi;
+        __syncthreads();
+        if (count <= kNarrowStage) {
+            // stage the bracket bin's values
+            if (threadIdx.x == 0) sh_i[0] = 0;
+            __syncthreads();
+            float* st = reinterpret_cast<float*>(scr);
+            each([&](float x, unsigned) {
+                const unsigned key = __float_as_uint(x);
+                if (key > klo && key <= khi) st[atomicAdd(sh_i, 1)] = x;
+            });
+            __syncthreads();
+            *m_st = (unsigned)sh_i[0];
+            __syncthreads();
+            return 0;
+        }
+    }
+    return 2;   // did not narrow enough (only float keys closer than 2^-20 relative could do this)
+}
+
 // Michelot's fixed point restricted to a window.  One whole block calls it.
 // n_hi, s_hi: count and sum of |x| > theta_hi; cand[0..m_raw): every |x| in
 // (theta_lo, theta_hi].  Returns 0 with *tau_out; 2 when the root lies above
@@ -37,51 +230,123 @@ struct WinInfo {
 // stage (optional): shared memory for stage_cap floats that the block no
 // longer uses; when the candidates fit they are copied there on the first
 // pass and every later pass reads them from it instead of from L2.
+// scr (optional): 3 kNarrowBins unsigned of shared memory; with more than
+// kNarrowMin candidates the window is first narrowed on the float keys
+// (l1_narrow; from the stage when they fit it, else from global memory), so
+// that Michelot's passes run over the few values of one narrow bin instead
+// of every candidate.
 static __device__ int l1_window_finish(double n_hi, double s_hi, const float* cand, unsigned m_raw,
                                        double theta_lo, double theta_hi, double r,
                                        double* tau_out, double* red_d,
                                        unsigned long long* red_u, WinInfo* info = nullptr,
-                                       float* stage = nullptr, unsigned stage_cap = 0) {
+                                       float* stage = nullptr, unsigned stage_cap = 0,
+                                       unsigned* scr = nullptr) {
     const double phi_hi = s_hi - n_hi * theta_hi - r;
     if (info) info->phi_hi = phi_hi;
     if (m_raw > kCandCap) return 1;
-    const unsigned m = m_raw;
+    unsigned m = m_raw;
     if (phi_hi > 0.0) return 2;                        // root above the window
+    if (scr && m > kNarrowMin && theta_lo >= 0.0) {
+        // the window's ends as float keys: (klo, khi] holds every candidate
+        unsigned klo = __float_as_uint((float)theta_lo), khi = __float_as_uint((float)theta_hi);
+        if ((double)__uint_as_float(klo) > theta_lo) klo -= 1u;        // rounding of the ends
+        if ((double)__uint_as_float(khi) < theta_hi) khi += 1u;
+        unsigned m_st = 0;
+        __shared__ int nr_i[1];
+        double nh = n_hi, sh = s_hi;
+        // with a stage that holds them, the candidates are read from global
+        // memory once and narrowed from shared memory
+        const float* src = cand;
+        bool src_shared = false;
+        if (stage && m <= stage_cap) {
+            for_each_candidate(cand, m, [&](float x, unsigned k) { stage[k] = x; });
+            __syncthreads();
+            src = stage;
+            src_shared = true;
+        }
+        // (red_d and red_u serve as the narrowing's scalars and warp totals)
+        const int rc = l1_narrow(src, src_shared, m, nh, sh, klo, khi, r, scr, &m_st, nr_i, red_d, red_u);
+        if (rc == 1) {
+            // phi(theta_lo) < 0: as below, inside the ball or a miss below
+            if (info) { info->phi_lo = red_d[2]; info->n_lo = red_d[3]; }
+            if (theta_lo <= 0.0) { *tau_out = 0.0; return 0; }
+            return 1;
+        }
+        if (rc == 0) {
+            // Michelot on the staged values of the bracket bin
+            n_hi = nh;
+            s_hi = sh;
+            cand = nullptr;
+            stage = reinterpret_cast<float*>(scr);
+            stage_cap = kNarrowStage;
+            m = m_st;
+            theta_lo = (double)__uint_as_float(klo);
+            theta_hi = (double)__uint_as_float(khi);
+            if (info) info = nullptr;                  // the window's own phi_lo is not computed here
+        }
+    }
     const bool staged = stage && m <= stage_cap;
+    const bool pre_staged = cand == nullptr;           // the narrowed values already sit in the stage
+    // Sums in compensated FP32 per thread and float pairs across the CTA;
+    // the FP64 steps (a handful per pass) run on thread 0 and reach the
+    // other threads through shared memory.
+    __shared__ float2 wf_pair[32];
+    __shared__ double wf_tau;
+    __shared__ float wf_tf;
+    __shared__ int wf_state;                          // 0 continue, 1 done, 2 inside, 3 below
     Kahan ks;
-    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-        const float x = __ldcg(cand + k);
-        if (staged) stage[k] = x;
-        ks.add(x);
+    if (pre_staged) {
+        for (unsigned k = threadIdx.x; k < m; k += blockDim.x) ks.add(stage[k]);
+    } else {
+        for_each_candidate(cand, m, [&](float x, unsigned k) {
+            if (staged) stage[k] = x;
+            ks.add(x);
+        });
     }
-    const double sum_c = block_sum(ks.value(), red_d);      // (its barriers publish the stage)
-    const double n_all = n_hi + (double)m;
-    const double phi_lo = s_hi + sum_c - n_all * theta_lo - r;
-    if (info) { info->phi_lo = phi_lo; info->n_lo = n_all; }
-    if (phi_lo < 0.0) {
-        if (theta_lo <= 0.0) { *tau_out = 0.0; return 0; }  // inside the ball
-        return 1;                                      // root below the window
+    const double sum_c = block_sum_pair(ks, wf_pair);       // (its barriers publish the stage)
+    if (threadIdx.x == 0) {
+        const double n_all = n_hi + (double)m;
+        const double phi_lo = s_hi + sum_c - n_all * theta_lo - r;
+        if (info) { info->phi_lo = phi_lo; info->n_lo = n_all; }
+        if (phi_lo < 0.0) {
+            wf_state = theta_lo <= 0.0 ? 2 : 3;
+        } else {
+            wf_state = 0;
+            wf_tau = (s_hi + sum_c - r) / n_all;
+            wf_tf = __double2float_rd(wf_tau);
+        }
     }
-    double tau = (s_hi + sum_c - r) / n_all;
+    __syncthreads();
+    const int st0 = wf_state;
+    if (st0 == 2) { *tau_out = 0.0; __syncthreads(); return 0; }   // inside the ball
+    if (st0 == 3) { __syncthreads(); return 1; }                    // root below the window
     unsigned long long prev = m;
     for (int it = 0; it < 200; ++it) {
         // for a float x, x > tau exactly when x > (tau rounded down to float):
-        // the test runs in FP32 (GB300's FP64 rate is a small fraction of it)
-        const float tf = __double2float_rd(tau);
+        // the test runs in FP32
+        const float tf = wf_tf;
         Kahan ka;
-        unsigned long long c = 0;
-        for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-            const float x = staged ? stage[k] : __ldcg(cand + k);
-            if (x > tf) { ka.add(x); ++c; }
+        unsigned c = 0;
+        auto take = [&](float x, unsigned) { if (x > tf) { ka.add(x); ++c; } };
+        if (staged) {
+            for (unsigned k = threadIdx.x; k < m; k += blockDim.x) take(stage[k], k);
+        } else {
+            for_each_candidate(cand, m, take);
         }
-        const double sa = block_sum(ka.value(), red_d);
-        const unsigned long long ca = block_sum(c, red_u);
-        const double tn = (s_hi + sa - r) / (n_hi + (double)ca);
-        tau = tn;
-        if (ca == prev) break;
+        const double sa = block_sum_pair(ka, wf_pair);
+        const unsigned long long ca = block_count(c, red_u);
+        if (threadIdx.x == 0) {
+            wf_tau = (s_hi + sa - r) / (n_hi + (double)ca);
+            wf_tf = __double2float_rd(wf_tau);
+            wf_state = ca == prev ? 1 : 0;
+        }
+        __syncthreads();
+        const bool done = wf_state == 1;
         prev = ca;
+        if (done) break;
     }
-    *tau_out = tau;
+    *tau_out = wf_tau;
+    __syncthreads();
     return 0;
 }
 
@@ -136,87 +401,97 @@ __host__ __device__ __forceinline__ bool hist_base_ok(unsigned hbase) {
     return hbase > 0u && ((unsigned long long)(hbase + kK1Bins) << kHistShift) < 0x7f800000ull;
 }
 
-// After K1's window missed: the bracket of the root that K1's histogram of
-// |x| gives.  hist: kK1Bins counts, bin b holding the |x| in [e_b, e_{b+1})
-// with e_b = hist_edge(hbase, b); n_top, s_top: count and sum of |x| >= e_top.
-// Taking every binned value at its bin's lower (upper) edge bounds phi at each
-// edge from below (above); the highest edge with phi >= 0 from below and the
-// lowest edge above it with phi < 0 from above bracket the root.  Returns 1
-// with the window (*lo, *hi] and the number of values inside it in *m, or 0
-// when the range does not bracket the root (or more than kCandCap values sit
-// in the bracket).  The bounds carry a relative margin, and the retry pass on
-// the window computes everything exactly, so a wrong bracket costs only time.
-// One whole block calls it; warp 0 works.
-static __device__ int l1_hist_bracket(const unsigned* hist, unsigned hbase, double n_top, double s_top,
-                                      double r, float* lo_out, float* hi_out, double* m_out, int* sh_i) {
+// After K1's window missed: a bracket of the root estimated from K1's sampled
+// histogram of |x|.  hist_g: kK1Bins counts of a 1/scale sample (global; hist:
+// kK1Bins unsigned of shared memory to read them into), bin b holding
+// the sampled |x| in [e_b, e_{b+1}) with e_b = hist_edge(hbase, b); n_top,
+// s_top: count and sum of the sampled |x| >= e_top.  Scaled up, and with every
+// binned value taken at its bin's lower (upper) edge, they estimate phi at each
+// edge from below (above); the highest edge whose lower estimate is >= 0 and
+// the lowest edge above it whose upper estimate is < 0 bracket the root, and
+// the bracket is widened by two bins on each side for the sampling error.
+// Returns 1 with the window (*lo, *hi] and the expected number of values
+// inside it in *m, or 0 when the range does not bracket the root or the
+// window would hold more than half of kCandCap values.  The retry pass on the
+// window computes everything exactly (a wrong bracket costs only time).  One
+// whole block calls it; warp 0 works.
+static __device__ int l1_hist_bracket(const unsigned* hist_g, unsigned hbase, double n_top, double s_top,
+                                      double r, double scale, float* lo_out, float* hi_out, double* m_out,
+                                      int* sh_i, unsigned* hist) {
     constexpr int PER = kK1Bins / 32;
+    constexpr int WIDEN = 2;
+    // the counts into shared memory (every thread, loads in parallel)
+    __syncthreads();
+    for (int k = threadIdx.x; k < kK1Bins; k += blockDim.x) hist[k] = __ldcg(hist_g + k);
     __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         const int b0 = lane * PER;
-        double c_l = 0.0, sl_l = 0.0, sh_l = 0.0;
+        // estimates from a sample: FP32 arithmetic is precise enough
+        const float fs = (float)scale;
+        const float nt_ = (float)(n_top * scale), st_ = (float)(s_top * scale), rf = (float)r;
+        float c_l = 0.f, sl_l = 0.f, sh_l = 0.f;
         for (int b = b0; b < b0 + PER; ++b) {
-            const double c = (double)__ldcg(hist + b);
+            const float c = fs * (float)hist[b];
             c_l += c;
-            sl_l += c * (double)hist_edge(hbase, b);
-            sh_l += c * (double)hist_edge(hbase, b + 1);
+            sl_l += c * hist_edge(hbase, b);
+            sh_l += c * hist_edge(hbase, b + 1);
         }
         // totals of the lanes above this one (exclusive suffix)
-        double c_in = c_l, sl_in = sl_l, sh_in = sh_l;
+        float c_in = c_l, sl_in = sl_l, sh_in = sh_l;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const double c = __shfl_down_sync(0xffffffffu, c_in, o);
-            const double a = __shfl_down_sync(0xffffffffu, sl_in, o);
-            const double b = __shfl_down_sync(0xffffffffu, sh_in, o);
+            const float c = __shfl_down_sync(0xffffffffu, c_in, o);
+            const float a = __shfl_down_sync(0xffffffffu, sl_in, o);
+            const float b = __shfl_down_sync(0xffffffffu, sh_in, o);
             if (lane + o < 32) { c_in += c; sl_in += a; sh_in += b; }
         }
-        const double total_sh = __shfl_sync(0xffffffffu, sh_in, 0);
-        // the float32-compensated sums carry about 1e-7 relative error
-        const double margin = 1e-6 * (s_top + total_sh + r);
-        const double top = (double)hist_edge(hbase, kK1Bins);
-        const double phi_top = s_top - n_top * top - r;         // exact up to the sums' rounding
-        // pass 1: the highest edge with phi >= margin from below
-        double N = n_top + (c_in - c_l), SL = s_top + (sl_in - sl_l);
-        int a_best = phi_top >= margin ? kK1Bins : -1;
+        const float top = hist_edge(hbase, kK1Bins);
+        const float phi_top = st_ - nt_ * top - rf;
+        // pass 1: the highest edge whose lower estimate is >= 0
+        float N = nt_ + (c_in - c_l), SL = st_ + (sl_in - sl_l);
+        int a_best = phi_top >= 0.f ? kK1Bins : -1;
         for (int b = b0 + PER - 1; b >= b0 && a_best < 0; --b) {
-            const double e = (double)hist_edge(hbase, b);
-            const double c = (double)__ldcg(hist + b);
+            const float e = hist_edge(hbase, b);
+            const float c = fs * (float)hist[b];
             N += c;
             SL += c * e;
-            if (SL - N * e - r >= margin) a_best = b;
+            if (SL - N * e - rf >= 0.f) a_best = b;
         }
         int a_all = a_best;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a_all = max(a_all, __shfl_xor_sync(0xffffffffu, a_all, o));
-        // pass 2: the lowest edge above it with phi < -margin from above
+        // pass 2: the lowest edge above it whose upper estimate is < 0
         int c_best = kK1Bins + 1;
         if (a_all >= 0 && a_all < kK1Bins) {
-            if (phi_top < -margin) c_best = kK1Bins;
-            N = n_top + (c_in - c_l);
-            double SH = s_top + (sh_in - sh_l);
+            if (phi_top < 0.f) c_best = kK1Bins;
+            N = nt_ + (c_in - c_l);
+            float SH = st_ + (sh_in - sh_l);
             for (int b = b0 + PER - 1; b >= b0; --b) {
-                const double e = (double)hist_edge(hbase, b);
-                const double c = (double)__ldcg(hist + b);
+                const float e = hist_edge(hbase, b);
+                const float c = fs * (float)hist[b];
                 N += c;
-                SH += c * (double)hist_edge(hbase, b + 1);
-                if (b > a_all && SH - N * e - r < -margin) c_best = b;   // the lowest such b of this lane
+                SH += c * hist_edge(hbase, b + 1);
+                if (b > a_all && SH - N * e - rf < 0.f) c_best = b;   // the lowest such b of this lane
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c_best = min(c_best, __shfl_xor_sync(0xffffffffu, c_best, o));
-        // values inside the bracket [e_a, e_c)
-        double m = 0.0;
-        if (a_all >= 0 && c_best <= kK1Bins)
+        const bool found = a_all >= 0 && a_all < kK1Bins && c_best <= kK1Bins;
+        const int lo_b = max(a_all - WIDEN, 0), hi_b = min(c_best + WIDEN, kK1Bins);
+        // expected values inside the widened bracket [e_lo, e_hi)
+        float m = 0.f;
+        if (found)
             for (int b = b0; b < b0 + PER; ++b)
-                if (b >= a_all && b < c_best) m += (double)__ldcg(hist + b);
+                if (b >= lo_b && b < hi_b) m += fs * (float)hist[b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
         if (lane == 0) {
-            const bool ok = a_all >= 0 && a_all < kK1Bins && c_best <= kK1Bins && m <= (double)kCandCap;
+            const bool ok = found && m <= 0.5f * (float)kCandCap;
             sh_i[0] = ok ? 1 : 0;
             if (ok) {
-                *lo_out = hist_edge(hbase, a_all);
-                *hi_out = hist_edge(hbase, c_best);
+                *lo_out = hist_edge(hbase, lo_b);
+                *hi_out = hist_edge(hbase, hi_b);
                 *m_out = m;
             }
         }
@@ -224,8 +499,6 @@ static __device__ int l1_hist_bracket(const unsigned* hist, unsigned hbase, doub
     __syncthreads();
     return sh_i[0];
 }
-
-
 
 // Records tau of this iteration and places the window of the next one around
 // the linear extrapolation of the last two thresholds.  After a window hit the

@@ -400,12 +400,10 @@ struct BlockCand {
     BlockCand name{name##_buf, name##_cnt, name##_base};         \
     name.init()
 
-// Gathers the bracket bin of every vector that needs it and finishes tau.
+// Gathers the bracket bin of every vector that needs it (k_search_finish
+// finishes tau).
 template <typename Src>
 __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a) {
-    __shared__ double red_d[64];
-    __shared__ unsigned long long red_u[64];
-    __shared__ int is_last;
     bool need[2];
     need[0] = a.sc->ctl[0].need == NEED_GATHER;
     need[1] = a.nvec > 1 && a.sc->ctl[1].need == NEED_GATHER;
@@ -418,47 +416,17 @@ __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a
         if (need[1]) bc.append(1, valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
     });
     bc.flush(a.w.cand, a.sc);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->g_ticket, 1u) == (unsigned)(a.total() - 1));
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    for (int v = 0; v < 2; ++v) {
-        if (!need[v]) continue;
-        L1Ctl& C = a.sc->ctl[v];
-        const double r = a.sc->radius[v];
-        const unsigned m = __ldcg(&a.sc->acc[v].m);
-        const double glo = C.g_lo, ghi = C.g_hi;
-        const double na = (double)C.n_above, sa = C.s_above;
-        double tau = 0.0;
-        const int rc = l1_window_finish(na, sa, a.w.cand[v], m, glo, ghi, r, &tau, red_d, red_u);
-        if (threadIdx.x == 0) {
-            if (rc == 2 && na > 0.0) {
-                // the root lies between the largest value of the bin and the
-                // next bin's edge: every value of the bin is inactive
-                tau = (sa - r) / na;
-            } else if (rc != 0) {
-                a.sc->error |= 2;
-            }
-            l1_record_tau(C, tau, (double)min(m, kCandCap), ghi - glo, false);
-            a.sc->acc[v].m = 0;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) a.sc->g_ticket = 0;
 }
 
 // One windowed pass after K1's window missed: count and sum of |x| above the
-// retry window, its values as candidates, then Michelot's finish; a second
-// miss leaves the threshold to the radix passes.  Per-CTA partial sums go to
-// pn / ps (the stencil pass's partial arrays, free by now).
+// retry window and its values as candidates (k_search_finish runs Michelot's
+// finish; a second miss leaves the threshold to the radix passes).  Per-CTA
+// partial sums go to pn / ps (the stencil pass's partial arrays, free by now).
 template <typename Src>
 __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a, unsigned long long* pn,
                                                double* ps) {
     __shared__ double red_d[64];
     __shared__ unsigned long long red_u[64];
-    __shared__ int is_last;
     bool need[2];
     need[0] = a.sc->ctl[0].need == NEED_WINDOW;
     need[1] = a.nvec > 1 && a.sc->ctl[1].need == NEED_WINDOW;
@@ -480,47 +448,81 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
         }
     });
     bc.flush(a.w.cand, a.sc);
+    float2* pbuf = reinterpret_cast<float2*>(red_d);
     const unsigned long long n0 = block_sum(w0.n, red_u), n1 = block_sum(w1.n, red_u);
-    const double s0 = block_sum(w0.s.value(), red_d), s1 = block_sum(w1.s.value(), red_d);
+    const double s0 = block_sum_pair(w0.s, pbuf), s1 = block_sum_pair(w1.s, pbuf);
     const int cta = a.cta_base + blockIdx.x;
     if (threadIdx.x == 0) {
         pn[2 * cta] = n0; pn[2 * cta + 1] = n1;
         ps[2 * cta] = s0; ps[2 * cta + 1] = s1;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->w_ticket, 1u) == (unsigned)(a.total() - 1));
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    for (int v = 0; v < 2; ++v) {
-        if (!need[v]) continue;
+}
+
+// The finish of the retry window (mode 0) or of the gathered radix bracket
+// (mode 1) for every vector that needs it: one CTA of kFinishThreads threads,
+// the candidates staged in its shared memory when they fit (kFinishStage
+// floats), narrowed on the float keys and finished by Michelot's step (see
+// l1_window_finish).  A single CTA walking a list of a few hundred thousand
+// candidates is bound by the latency of its loads, so it runs apart from the
+// main pass with the most threads a CTA can have.  parts: the main pass's
+// CTAs (mode 0: their count and sum above the window in pn / ps).
+constexpr int kFinishThreads = 1024;
+constexpr unsigned kFinishStage = 32768;
+constexpr size_t kFinishSmem = kFinishStage * sizeof(float) + 3 * kNarrowBins * sizeof(unsigned);
+__global__ void __launch_bounds__(kFinishThreads) k_search_finish(const SearchArgs a, int mode,
+                                                                   const unsigned long long* pn,
+                                                                   const double* ps, int parts) {
+    extern __shared__ __align__(16) float fstage[];         // kFinishStage floats + the narrowing scratch
+    __shared__ double red_d[64];
+    __shared__ unsigned long long red_u[64];
+    const int want = mode == 0 ? NEED_WINDOW : NEED_GATHER;
+    unsigned* scr = reinterpret_cast<unsigned*>(fstage + kFinishStage);
+    for (int v = 0; v < a.nvec; ++v) {
         L1Ctl& C = a.sc->ctl[v];
-        unsigned long long n = 0;
-        double sm = 0.0;
-        for (int k = threadIdx.x; k < a.total(); k += NT) {
-            n += __ldcg(pn + 2 * k + v);
-            sm += __ldcg(ps + 2 * k + v);
-        }
-        n = block_sum(n, red_u);
-        sm = block_sum(sm, red_d);
+        if (C.need != want) continue;                       // uniform over the CTA
+        const double r = a.sc->radius[v];
         const unsigned m = __ldcg(&a.sc->acc[v].m);
         const double lo = C.g_lo, hi = C.g_hi;
+        double n = 0.0, sm = 0.0;
+        if (mode == 0) {
+            unsigned long long nn = 0;
+            double ss = 0.0;
+            for (int k = threadIdx.x; k < parts; k += blockDim.x) {
+                nn += __ldcg(pn + 2 * k + v);
+                ss += __ldcg(ps + 2 * k + v);
+            }
+            n = (double)block_sum(nn, red_u);
+            sm = block_sum(ss, red_d);
+        } else {
+            n = (double)C.n_above;
+            sm = C.s_above;
+        }
         double tau = 0.0;
-        const int rc = l1_window_finish((double)n, sm, a.w.cand[v], m, lo, hi, a.sc->radius[v], &tau, red_d, red_u);
+        const int rc = l1_window_finish(n, sm, a.w.cand[v], m, lo, hi, r, &tau, red_d, red_u, nullptr, fstage,
+                                        kFinishStage, scr);
         if (threadIdx.x == 0) {
-            if (rc == 0) {
-                l1_record_tau(C, tau, (double)min(m, kCandCap), hi - lo, false);
-                C.retry_hits++;
+            if (mode == 0) {
+                if (rc == 0) {
+                    l1_record_tau(C, tau, (double)min(m, kCandCap), hi - lo, false);
+                    C.retry_hits++;
+                } else {
+                    C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0;
+                    C.exact_runs++;
+                }
             } else {
-                C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0;
-                C.exact_runs++;
+                if (rc == 2 && n > 0.0) {
+                    // the root lies between the largest value of the bin and
+                    // the next bin's edge: every value of the bin is inactive
+                    tau = (sm - r) / n;
+                } else if (rc != 0) {
+                    a.sc->error |= 2;
+                }
+                l1_record_tau(C, tau, (double)min(m, kCandCap), hi - lo, false);
             }
             a.sc->acc[v].m = 0;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) a.sc->w_ticket = 0;
 }
 
 // out = soft(x, tau) for the standalone projection
@@ -754,7 +756,16 @@ int light_configure(int storage) {
     }
     if (e != cudaSuccess) return -3;
     e = cudaFuncSetAttribute(k_radix<FlatSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return -3;
+    e = cudaFuncSetAttribute(k_search_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinishSmem);
     return e == cudaSuccess ? 0 : -3;
+}
+
+int launch_search_finish(int mode, Scal* sc, const L1Work& w, int nvec, const unsigned long long* pn,
+                         const double* ps, int parts, cudaStream_t st) {
+    SearchArgs a{sc, w, nvec};
+    k_search_finish<<<1, kFinishThreads, kFinishSmem, st>>>(a, mode, pn, ps, parts);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int k2_grid_ctas(const Geom& g) { return k2_grid_part(g, whole_cube(g)); }
@@ -920,6 +931,7 @@ int l1_project_standalone(const float* x, long long n, double radius, float* out
         for (int level = 0; level < 3 && rc == 0; ++level) rc = launch_radix_src(src, n, a, level, st);
         if (rc == 0) {
             k_gather<FlatSrc><<<gather_grid_n(n), NT, 0, st>>>(src, a);
+            k_search_finish<<<1, kFinishThreads, kFinishSmem, st>>>(a, 1, nullptr, nullptr, 0);
             k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
             if (cudaGetLastError() != cudaSuccess) rc = -3;
         }
@@ -1018,6 +1030,7 @@ int l1_project_noalloc(const float* x, long long n, double radius, float* out, d
     for (int level = 0; level < 3; ++level)
         if (launch_radix_src(src, n, a, level, st) != 0) return -3;
     k_gather<FlatSrc><<<gather_grid_n(n), NT, 0, st>>>(src, a);
+    k_search_finish<<<1, kFinishThreads, kFinishSmem, st>>>(a, 1, nullptr, nullptr, 0);
     k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
     if (cudaGetLastError() != cudaSuccess) return -3;
     double t = 0.0;

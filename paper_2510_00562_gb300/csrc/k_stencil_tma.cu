@@ -109,7 +109,9 @@ struct Lay {
     // one-pixel ring: w positions 2 (TX + 2) + 2 TY per set, u' positions (TX + 1) + TY
     static constexpr int NWR = 2 * (TX + 2) + 2 * TY, NUR = (TX + 1) + TY;
     static_assert(TY * TX == NT, "one tile voxel per thread");
-    static_assert(SMEM + 1200 <= 227 * 1024, "shared memory");
+    // dynamic plus the kernel's static shared memory (reductions and the
+    // threshold finish: about 1.4 KB, see ptxas -v) within the 227 KB a CTA may use
+    static_assert(SMEM + 1536 <= 227 * 1024, "shared memory");
     static_assert(2 * NWR <= 224 && NUR <= 32 + 32, "ring work layout");
 };
 
@@ -164,41 +166,6 @@ __device__ __forceinline__ void append_shared(bool take, float x, float* buf, un
     if (base + __popc(mask) > (unsigned)Lay::CB) append_candidate(take && k >= (unsigned)Lay::CB, x, cand, gcnt);
 }
 
-// Sum over the CTA of the threads' compensated sums, carried as unevaluated
-// float pairs (hi + lo, Knuth's two-sum at every step) so that no FP64
-// instruction runs per warp; the pair becomes a double on thread 0 only.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void pair_add(float& hi, float& lo, float bhi, float blo) {
-    float s, e;
-    two_sum(hi, bhi, s, e);
-    e = __fadd_rn(e, __fadd_rn(lo, blo));
-    hi = __fadd_rn(s, e);
-    lo = __fsub_rn(e, __fsub_rn(hi, s));
-}
-__device__ double block_sum_pair(const Kahan& k, float2* buf) {
-    float hi = k.s, lo = -k.c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
-        pair_add(hi, lo, bh, bl);
-    }
-    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) buf[w] = make_float2(hi, lo);
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        float h = buf[0].x, l = buf[0].y;
-        for (int k2 = 1; k2 < nw; ++k2) pair_add(h, l, buf[k2].x, buf[k2].y);
-        r = (double)h + (double)l;
-    }
-    return r;
-}
-
 // Counts x into a window accumulator when `take`, without a branch.
 __device__ __forceinline__ void win_add(K1Acc& A, bool take, float x) {
     Kahan k = A.s;
@@ -216,7 +183,10 @@ __device__ __forceinline__ void hist_add(bool on, float x, unsigned hb, unsigned
     const unsigned bin = kb - hb;                    // below the range wraps to a large value
     const bool in = on && bin < (unsigned)kK1Bins;
     if (in) atomicAdd(h + (bin >> 1), (bin & 1u) ? 65536u : 1u);
-    win_add(top, on && !in && kb >= hb + (unsigned)kK1Bins, x);
+    // above the range: an estimate from a sample, a plain sum suffices
+    const bool up = on && !in && kb >= hb + (unsigned)kK1Bins;
+    top.n += up ? 1u : 0u;
+    top.s.s += up ? x : 0.f;
 }
 
 // value of a set selector: an int, or a std::integral_constant
@@ -239,7 +209,7 @@ using Set1 = std::integral_constant<int, 1>;
 using Store = std::true_type;
 using NoStore = std::false_type;
 
-template <bool EDGE>
+template <bool EDGE, bool HIST>
 __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsigned char* sm, unsigned* ccnt,
                                         int i0, int j0, int b0, int b1, K1State& S, const K1Win& W, float cs) {
     using L = Lay;
@@ -482,7 +452,7 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     };
 
     // ---- l1 window statistics of s~, t~ at this thread's voxel ----
-    auto stats = [&](const float* ys) {
+    auto stats = [&](const float* ys, int b) {
         float xs = 0.f, xt = 0.f;
         if (valid_t) {
             // s~ = s - g_s y4, t~ = t - g_t (D_v^T y3 + y4), each product and
@@ -508,9 +478,13 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
             append_shared(cs_, x_s, cbuf, ccnt, a.l1.cand[0], &a.sc->acc[0].m);
             append_shared(ct_, x_t, cbuf + L::CB, ccnt + 1, a.l1.cand[1], &a.sc->acc[1].m);
         }
-        if (W.hs || W.ht) {                               // the same for every thread
-            hist_add(W.hs && valid_t, x_s, W.hb_s, hsm, S.top_s);
-            hist_add(W.ht && valid_t, x_t, W.hb_t, hsm + kK1Bins / 2, S.top_t);
+        if constexpr (HIST) {
+            // one voxel per warp and band (the lane rotates with the band and
+            // the warp) goes into the histogram: a 1/32 sample spread over the
+            // tile's rows, and no two lanes of a warp contend for one counter
+            const bool samp = valid_t && (threadIdx.x & 31) == ((unsigned)(b * 13 + (tid >> 5) * 7) & 31u);
+            hist_add(W.hs && samp, x_s, W.hb_s, hsm, S.top_s);
+            hist_add(W.ht && samp, x_t, W.hb_t, hsm + kK1Bins / 2, S.top_t);
         }
     };
 
@@ -564,7 +538,7 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
             float ycur[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) ycur[k] = ys[k * YPL + ky_t];
-            if (W.s || W.t) stats(ys);
+            if (W.s || W.t) stats(ys, b);
             w_item(Set0{}, Store{}, ys, wst, r_t, c_t, a.w1_n + ob, valid_t);
             w_item(Set1{}, Store{}, ys, wst, r_t, c_t, a.w2_n + ob, valid_t);
             u_item(Store{}, ysn, upn, b + 1, r_t, c_t, a.u_n + (ob + plane), valid_t && b + 1 < b1);
@@ -626,8 +600,11 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
 
     K1State S;
     const bool edge = !(i0 >= 2 && i0 + L::TY + 3 <= g.n1 && j0 >= 2 && j0 + L::TX + 3 <= g.n2);
-    const bool ok = edge ? k1_tile<true>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs)
-                         : k1_tile<false>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs);
+    const bool hist = W.hs || W.ht;
+    const bool ok = edge ? (hist ? k1_tile<true, true>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs)
+                                 : k1_tile<true, false>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs))
+                         : (hist ? k1_tile<false, true>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs)
+                                 : k1_tile<false, false>(maps, a, sm, ccnt, i0, j0, b0, b1, S, W, cs));
     if (!ok) {
         // a load never arrived: record it, let this CTA's copies land (bounded)
         // before its shared memory is released, and skip the statistics (the
@@ -660,17 +637,6 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
             for (unsigned k = tid; k < n; k += L::NT)
                 if (cbase[v] + k < kCandCap) a.l1.cand[v][cbase[v] + k] = cbuf[v * L::CB + k];
         }
-        float2* pbuf = reinterpret_cast<float2*>(red_d);
-        const unsigned long long ns = block_sum((unsigned long long)S.acc_s.n, red_u);
-        const double ss = block_sum_pair(S.acc_s.s, pbuf);
-        const unsigned long long nt = block_sum((unsigned long long)S.acc_t.n, red_u);
-        const double st = block_sum_pair(S.acc_t.s, pbuf);
-        if (tid == 0) {
-            a.l1.k1_n[4 * cta] = ns;
-            a.l1.k1_n[4 * cta + 1] = nt;
-            a.l1.k1_s[4 * cta] = ss;
-            a.l1.k1_s[4 * cta + 1] = st;
-        }
         if (W.hs || W.ht) {
             // the histogram joins the global one (unpacked, nonzero bins only)
             const unsigned* hsm = reinterpret_cast<const unsigned*>(sm + L::OFF_HIST);
@@ -681,15 +647,45 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
                 if (w & 0xffffu) atomicAdd(gh, w & 0xffffu);
                 if (w >> 16) atomicAdd(gh + 1, w >> 16);
             }
-            const unsigned long long hn_s = block_sum((unsigned long long)S.top_s.n, red_u);
-            const double hs_s = block_sum_pair(S.top_s.s, pbuf);
-            const unsigned long long hn_t = block_sum((unsigned long long)S.top_t.n, red_u);
-            const double hs_t = block_sum_pair(S.top_t.s, pbuf);
-            if (tid == 0) {
-                a.l1.k1_n[4 * cta + 2] = hn_s;
-                a.l1.k1_n[4 * cta + 3] = hn_t;
-                a.l1.k1_s[4 * cta + 2] = hs_s;
-                a.l1.k1_s[4 * cta + 3] = hs_t;
+        }
+        // the CTA's window statistics (counts and sums above the windows) and
+        // the histograms' above-range statistics, reduced together: 32-bit
+        // counts and float-pair sums through the warps, one barrier, thread 0
+        // finishes (no FP64 outside thread 0)
+        unsigned n4[4] = {S.acc_s.n, S.acc_t.n, S.top_s.n, S.top_t.n};
+        float hi4[4] = {S.acc_s.s.s, S.acc_t.s.s, S.top_s.s.s, S.top_t.s.s};
+        float lo4[4] = {-S.acc_s.s.c, -S.acc_t.s.c, -S.top_s.s.c, -S.top_t.s.c};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                n4[q] += __shfl_xor_sync(0xffffffffu, n4[q], o);
+                const float bh = __shfl_xor_sync(0xffffffffu, hi4[q], o), bl = __shfl_xor_sync(0xffffffffu, lo4[q], o);
+                pair_add(hi4[q], lo4[q], bh, bl);
+            }
+        }
+        float* wbuf = reinterpret_cast<float*>(sm + L::OFF_G);          // idle now: 16 warps x 12 values
+        if ((tid & 31) == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                wbuf[(tid >> 5) * 12 + q] = __uint_as_float(n4[q]);
+                wbuf[(tid >> 5) * 12 + 4 + q] = hi4[q];
+                wbuf[(tid >> 5) * 12 + 8 + q] = lo4[q];
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                unsigned long long n = 0;
+                float h = wbuf[4 + q], l = wbuf[8 + q];
+                n += __float_as_uint(wbuf[q]);
+                for (int w = 1; w < L::NT / 32; ++w) {
+                    n += __float_as_uint(wbuf[w * 12 + q]);
+                    pair_add(h, l, wbuf[w * 12 + 4 + q], wbuf[w * 12 + 8 + q]);
+                }
+                a.l1.k1_n[4 * cta + q] = n;
+                a.l1.k1_s[4 * cta + q] = (double)h + (double)l;
             }
         }
     }
@@ -730,9 +726,12 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
         const double tlo = C.theta_lo, thi = C.theta_hi;
         double tau = 0.0;
         WinInfo wi;
-        // the tile's shared memory (up to the mbarriers) is idle now: stage the candidates there
+        // the tile's shared memory below the histogram is idle now: a stage
+        // for the candidates and the narrowing scratch at its end
+        constexpr int kScr = 3 * kNarrowBins * 4;
         const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi,
-                                          reinterpret_cast<float*>(sm), L::OFF_HIST / 4);
+                                          reinterpret_cast<float*>(sm), (L::OFF_HIST - kScr) / 4,
+                                          reinterpret_cast<unsigned*>(sm + L::OFF_HIST - kScr));
         // after a miss, the histogram (when on) brackets the root for one
         // retry pass over the bracket
         const bool hist_v = v == 0 ? W.hs : W.ht;
@@ -749,7 +748,8 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
             hn = block_sum(hn, red_u);
             hs = block_sum(hs, red_d);
             hist_hit = l1_hist_bracket(a.l1.khist + v * kK1Bins, v == 0 ? W.hb_s : W.hb_t, (double)hn, hs, r,
-                                       &h_lo, &h_hi, &h_m, &sh_flag);
+                                       (double)kHistSample, &h_lo, &h_hi, &h_m, &sh_flag,
+                                       reinterpret_cast<unsigned*>(sm + L::OFF_HIST));
         }
         if (hist_v) {
             __syncthreads();
