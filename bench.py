@@ -518,8 +518,9 @@ def run_batch(args):
     """Many uneven cubes, each with its own Eq. 28 stopping rule (< 1e-5, at
     most 3000 passes): the batch solver against looping the plain solver over
     the same cubes.  One JSON line."""
-    # more hardware work queues than the default 8, so that the cubes' streams
-    # do not share queues (read when the CUDA context is created)
+    # more hardware work queues than the default 8, so that the streams of the
+    # one-stream-per-cube batch do not share queues (read when the CUDA context
+    # is created)
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import numpy as np
     import torch
@@ -544,9 +545,17 @@ def run_batch(args):
         torch.cuda.synchronize()
         return r, time.perf_counter() - t0
 
+    # the batch with one stream per cube (the path 16-bit cubes take)
+    os.environ["GSSTV_BATCH"] = "streams"
+    with GeoSSTVBatch(shapes, params) as bs:
+        del os.environ["GSSTV_BATCH"]
+        bs.solve(vs)
+        (us_s, _, _, done_s), t_streams = timed(lambda: bs.solve(vs))
     with GeoSSTVBatch(shapes, params) as bt:
         bt.solve(vs)                                     # graphs built
         (us, _, _, done_b), t_batch = timed(lambda: bt.solve(vs))
+        d_streams = max(float((a - b).abs().max().item()) for a, b in zip(us_s, us))
+        del us_s
         # the same batch with every cube's band runs chosen by measurement
         chunks, t_tune = timed(lambda: bt.autotune(vs, passes=20))
         bt.solve(vs)                                     # graphs built again
@@ -574,6 +583,10 @@ def run_batch(args):
         "voxels": float(vox.sum()), "passes": {"min": int(min(done_b)), "median": float(np.median(done_b)),
                                                "max": int(max(done_b))},
         "batch_s": t_batch, "batch_value": vi_b / t_batch,
+        "launch": "every stage one launch over all cubes (a table of the cubes' first CTAs), device-side "
+                  "stopping rules, 16 passes per CUDA graph",
+        "streams_s": t_streams, "streams_same_passes": list(done_s) == list(done_b),
+        "max_abs_u_diff_streams": d_streams,
         "loop_s": t_loop, "loop_value": vi_l / t_loop, "unit": UNIT,
         "speedup": t_loop / t_batch, "same_passes": list(done_b) == list(done_l),
         "max_abs_u_diff": dmax,

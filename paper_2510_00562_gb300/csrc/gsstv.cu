@@ -134,6 +134,10 @@ IterParams iparams(const gsstv_handle* h, int par) {
     ip.eps = p.eps;
     ip.parity = par;
     ip.tau_exact = p.tau_mode == GSSTV_TAU_EXACT;
+    ip.max_iter = 0;                   // the stopping rule runs on the host for a single handle
+    ip.check_every = 0;
+    ip.tol = 0.0;
+    ip.live = nullptr;
     return ip;
 }
 
@@ -756,10 +760,25 @@ struct gsstv_batch {
     std::vector<cudaEvent_t> ev;
     Scal* pinned = nullptr;        // one Scal per cube, page-locked
     cudaStream_t caller = nullptr;
+    // one launch per stage for every cube (float32 cubes, at most kBatchMax)
+    bool fused = false;
+    K1Maps* dmaps = nullptr;       // [cube][parity] tensor maps in device memory
+    int* live = nullptr;           // device: cubes still iterating
+    int* live_host = nullptr;      // page-locked copy
+    cudaStream_t cap = nullptr;    // private capture stream
+    cudaGraphExec_t gexec = nullptr;
+    int graph_len = 0;
+    std::vector<int> graph_chunks;  // the cubes' K1 band runs the graph was built with
 };
 
 int gsstv_batch_destroy(gsstv_batch* b) {
     if (!b) return GSSTV_OK;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->caller) cudaStreamSynchronize(b->caller);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->dmaps) cudaFree(b->dmaps);
+    if (b->live) cudaFree(b->live);
+    if (b->live_host) cudaFreeHost(b->live_host);
     for (gsstv_handle* h : b->h) gsstv_destroy(h);
     for (cudaEvent_t e : b->ev) if (e) cudaEventDestroy(e);
     for (cudaStream_t s : b->st) if (s) cudaStreamDestroy(s);
@@ -795,12 +814,144 @@ int gsstv_batch_create(gsstv_batch** out, int ncubes, const int* n1, const int* 
         rc = gsstv_create(&h, n1[c], n2[c], n3[c], &params[c], s);
         if (rc == GSSTV_OK) b->h.push_back(h);
     }
+    // Float32 cubes run every stage of a pass as one launch over all cubes
+    // (GSSTV_BATCH=streams keeps one stream per cube, as 16-bit cubes do).
+    if (rc == GSSTV_OK) {
+        const char* ev = std::getenv("GSSTV_BATCH");
+        b->fused = ncubes <= kBatchMax && !(ev && std::strcmp(ev, "streams") == 0);
+        for (gsstv_handle* h : b->h)
+            if (h->p.storage != GSSTV_FP32 || h->k1_variant != 1) b->fused = false;
+    }
+    if (rc == GSSTV_OK && b->fused) {
+        if (batch_configure() != 0) rc = GSSTV_ERR_CUDA;
+        if (rc == GSSTV_OK && cudaMalloc((void**)&b->dmaps, sizeof(K1Maps) * 2 * ncubes) != cudaSuccess) {
+            cudaGetLastError();
+            b->dmaps = nullptr;
+            rc = GSSTV_ERR_OOM;
+        }
+        if (rc == GSSTV_OK && cudaMalloc((void**)&b->live, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            b->live = nullptr;
+            rc = GSSTV_ERR_OOM;
+        }
+        if (rc == GSSTV_OK && cudaMallocHost((void**)&b->live_host, sizeof(int)) != cudaSuccess) {
+            b->live_host = nullptr;
+            rc = GSSTV_ERR_OOM;
+        }
+        if (rc == GSSTV_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+            b->cap = nullptr;
+            rc = GSSTV_ERR_CUDA;
+        }
+        for (int c = 0; c < ncubes && rc == GSSTV_OK; ++c)
+            rc = cuda_rc(cudaMemcpy(b->dmaps + 2 * c, b->h[c]->maps, 2 * sizeof(K1Maps), cudaMemcpyHostToDevice));
+    }
     if (rc != GSSTV_OK) { gsstv_batch_destroy(b); return rc; }
     *out = b;
     return GSSTV_OK;
 }
 
 int gsstv_batch_size(const gsstv_batch* b) { return b ? (int)b->h.size() : 0; }
+
+namespace {
+
+// One pass of every unfinished cube from parity `par`: each stage one launch.
+int batch_enqueue(gsstv_batch* b, int par, cudaStream_t st) {
+    const int nc = (int)b->h.size();
+    BatchCube cubes[kBatchMax];
+    for (int c = 0; c < nc; ++c) {
+        gsstv_handle* h = b->h[c];
+        BatchCube& q = cubes[c];
+        q.g = h->g;
+        q.b = bufs(h, par);
+        q.p = iparams(h, par);
+        q.p.max_iter = h->p.max_iter;          // the stopping rule on the device
+        q.p.tol = h->p.tol;
+        q.p.check_every = h->p.check_every;
+        q.p.live = b->live;
+        q.sc = h->sc;
+        q.l1 = h->l1;
+        q.k2_part = h->k2_part;
+        q.k2_cap = h->k2_cap;
+        q.k1_chunk = h->k1_chunk;
+        q.k1_ctas = h->k1_ctas;
+        q.maps = b->dmaps + 2 * c + par;
+    }
+    TRY(map_launch(launch_k1_batch(cubes, nc, st)));
+    TRY(map_launch(launch_window_batch(cubes, nc, st)));
+    TRY(map_launch(launch_finish_batch(cubes, nc, 0, st)));
+    for (int level = 0; level < 3; ++level) TRY(map_launch(launch_radix_batch(cubes, nc, level, st)));
+    TRY(map_launch(launch_gather_batch(cubes, nc, st)));
+    TRY(map_launch(launch_finish_batch(cubes, nc, 1, st)));
+    TRY(map_launch(launch_k2_batch(cubes, nc, st)));
+    return GSSTV_OK;
+}
+
+// The fused solve: every cube from its standard start, blocks of passes as
+// one CUDA graph (even length: the parity comes back to 0) until no cube is
+// left iterating.  A cube stops on the device at the pass its own stopping
+// rule names, exactly as gsstv_iterate stops it (Eq. 28 every check_every
+// passes, or max_iter).
+int batch_solve_fused(gsstv_batch* b, const float* const* d_v, float* const* d_u, float* const* d_s,
+                      float* const* d_t, int* iters_done) {
+    const int nc = (int)b->h.size();
+    int live = 0, most = 0;
+    for (int c = 0; c < nc; ++c) {
+        gsstv_handle* h = b->h[c];
+        TRY(gsstv_load_observation(h, d_v[c]));
+        TRY(gsstv_reset_state(h));                       // synchronises the cube's stream
+        if (h->p.max_iter > 0) {
+            ++live;
+            most = std::max(most, h->p.max_iter);
+        } else {                                         // nothing to run: stopped at the start
+            const int one[2] = {1, 0};
+            TRY(cuda_rc(cudaMemcpy(&h->sc->done, one, sizeof(one), cudaMemcpyHostToDevice)));
+        }
+    }
+    TRY(cuda_rc(cudaMemcpyAsync(b->live, &live, sizeof(int), cudaMemcpyHostToDevice, b->caller)));
+    const int G = 16;
+    std::vector<int> chunks(nc);
+    for (int c = 0; c < nc; ++c) chunks[c] = b->h[c]->k1_chunk;   // (the autotuner may change them)
+    if (!b->gexec || b->graph_len != G || chunks != b->graph_chunks) {
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        TRY(cuda_rc(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)));
+        int rc = GSSTV_OK;
+        for (int k = 0; k < G && rc == GSSTV_OK; ++k) rc = batch_enqueue(b, k & 1, b->cap);
+        const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+        if (rc != GSSTV_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        TRY(cuda_rc(e));
+        const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        TRY(cuda_rc(ei));
+        b->graph_len = G;
+        b->graph_chunks = chunks;
+    }
+    for (int run = 0; live > 0 && run < most; run += G) {
+        TRY(cuda_rc(cudaGraphLaunch(b->gexec, b->caller)));
+        TRY(cuda_rc(cudaMemcpyAsync(b->live_host, b->live, sizeof(int), cudaMemcpyDeviceToHost, b->caller)));
+        TRY(cuda_rc(cudaStreamSynchronize(b->caller)));
+        live = *b->live_host;
+    }
+    int rc = GSSTV_OK;
+    for (int c = 0; c < nc && rc == GSSTV_OK; ++c) {
+        gsstv_handle* h = b->h[c];
+        Scal s;
+        rc = read_scalars(h, &s);
+        if (rc == GSSTV_OK) rc = error_of(s);
+        if (rc != GSSTV_OK) break;
+        h->parity = s.done ? s.stop_parity : 0;
+        h->stats.iterations += s.iter;
+        h->stats.last_rel_change = s.u2 > 0 ? std::sqrt(s.du2 / s.u2) : INFINITY;
+        h->stats.last_tau_s = s.ctl[0].tau;
+        h->stats.last_tau_t = s.ctl[1].tau;
+        h->stats.last_l2_scale = s.c[h->parity];
+        if (iters_done) iters_done[c] = (int)s.iter;
+        rc = copy_out_device(h, d_u[c], d_s ? d_s[c] : nullptr, d_t ? d_t[c] : nullptr);
+    }
+    return rc;
+}
+
+}  // namespace
 
 int gsstv_batch_solve(gsstv_batch* b, const float* const* d_v, float* const* d_u, float* const* d_s,
                       float* const* d_t, int* iters_done) {
@@ -809,6 +960,7 @@ int gsstv_batch_solve(gsstv_batch* b, const float* const* d_v, float* const* d_u
     for (int c = 0; c < nc; ++c) if (!d_v[c] || !d_u[c]) return GSSTV_ERR_ARG;
     // the inputs were written on the caller's stream
     TRY(cuda_rc(cudaStreamSynchronize(b->caller)));
+    if (b->fused) return batch_solve_fused(b, d_v, d_u, d_s, d_t, iters_done);
     std::vector<int> done(nc, 0), left(nc, 0), busy(nc, 0), over(nc, 0);
     int rc = GSSTV_OK;
     auto launch_block = [&](int c) {

@@ -156,6 +156,8 @@ struct Scal {
     int pad0;
     double q2, du2, u2;        // norms of the last K2 pass
     long long iter;
+    int done;                  // a batch cube that has stopped (Eq. 28 or its pass cap)
+    int stop_parity;           // the parity that holds its state then
 };
 
 constexpr int kHistBins = 2048;        // radix histogram bins per vector
@@ -349,6 +351,11 @@ struct IterParams {
     double eps;
     int parity;                  // iteration parity (selects c[])
     int tau_exact;               // 1: skip the window statistics
+    // the stopping rule applied on the device (batch cubes; max_iter = 0: off)
+    int max_iter;
+    int check_every;
+    double tol;
+    int* live;                   // counter of the batch's unfinished cubes
 };
 
 // Tensor maps over the current-parity buffers read by the TMA-fed K1.
@@ -412,6 +419,36 @@ int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p
 int launch_search_finish(int mode, Scal* sc, const L1Work& w, int nvec, const unsigned long long* pn,
                          const double* ps, int parts, cudaStream_t st);
 int k2_grid_ctas(const Geom& g);
+
+// ---------------------------------------------------------------------------
+// batches: every stage of a pass launched once for many independent cubes
+// ---------------------------------------------------------------------------
+// What a batch launch needs of one cube at one iteration parity.  Each cube
+// keeps its own state, reductions and stopping rule (IterParams max_iter, tol,
+// check_every: K2 sets Scal::done on the device); a launch covers the CTAs of
+// every cube, each CTA finds its cube in a table of first CTAs, and the CTAs
+// of a cube that is done return at once.  Float32 storage.
+constexpr int kBatchMax = 64;
+struct BatchCube {
+    Geom g;
+    IterBufs b;
+    IterParams p;
+    Scal* sc;
+    L1Work l1;
+    double* k2_part;
+    int k2_cap;
+    int k1_chunk;            // bands per K1 CTA (as the cube's handle runs it)
+    int k1_ctas;             // capacity of the cube's per-CTA statistics
+    const K1Maps* maps;      // the cube's tensor maps at this parity (device memory)
+};
+// Each launches one stage for cubes[0..n) on st (n <= kBatchMax).
+int launch_k1_batch(const BatchCube* cubes, int n, cudaStream_t st);
+int launch_window_batch(const BatchCube* cubes, int n, cudaStream_t st);
+int launch_radix_batch(const BatchCube* cubes, int n, int level, cudaStream_t st);
+int launch_gather_batch(const BatchCube* cubes, int n, cudaStream_t st);
+int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st);
+int launch_k2_batch(const BatchCube* cubes, int n, cudaStream_t st);
+int batch_configure();
 
 // float32 cubes between two layouts: ncubes cubes of nbands x n1 rows of n2
 // values, source and destination each with its own row pitch and cube stride

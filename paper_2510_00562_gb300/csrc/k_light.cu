@@ -91,8 +91,10 @@ struct K2Args {
     SlabPart sp;        // the bands updated, and this launch's CTAs among the stage's
 };
 
+// The CTA `bid` of `nblk` that share one cube's K2 (a launch of its own, or
+// the cube's share of a batch launch).
 template <typename T>
-__global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
+__device__ __forceinline__ void k2_body(const K2Args<T>& a, const int bid, const int nblk) {
     __shared__ double red_d[64];
     __shared__ int is_last;
     const Geom g = a.g;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
     const int strips = (g.n1 + K2_ROWS - 1) / K2_ROWS;
     const long long items = (long long)(a.sp.o1 - a.sp.o0) * strips * quads;
     Kahan aq, adu, au;
-    for (long long it = blockIdx.x * (long long)NT + threadIdx.x; it < items; it += (long long)gridDim.x * NT) {
+    for (long long it = bid * (long long)NT + threadIdx.x; it < items; it += (long long)nblk * NT) {
         const int qd = (int)(it % quads);
         const long long rest = it / quads;
         const int strip = (int)(rest % strips);
@@ -176,8 +178,8 @@ __global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
     const double q2 = block_sum(aq.value(), red_d);
     const double du2 = block_sum(adu.value(), red_d);
     const double u2 = block_sum(au.value(), red_d);
-    const int cta = a.sp.cta_base + blockIdx.x;
-    const int ncta = a.sp.cta_total > 0 ? a.sp.cta_total : (int)gridDim.x;
+    const int cta = a.sp.cta_base + bid;
+    const int ncta = a.sp.cta_total > 0 ? a.sp.cta_total : nblk;
     if (threadIdx.x == 0) {
         a.part[3 * cta] = q2;
         a.part[3 * cta + 1] = du2;
@@ -212,7 +214,23 @@ __global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
         sc->u2 = s2;
         sc->iter++;
         sc->k2_ticket = 0;
+        // the stopping rule of a batch cube (Eq. 28, or the pass cap): on the
+        // device, so that a batch runs as one graph without host polling
+        if (P.max_iter > 0) {
+            const bool at_check = P.tol > 0.0 && P.check_every > 0 && sc->iter % P.check_every == 0;
+            const bool conv = at_check && s2 > 0.0 && sqrt(s1 / s2) < P.tol;
+            if (conv || sc->iter >= P.max_iter) {
+                sc->done = 1;
+                sc->stop_parity = P.parity ^ 1;
+                if (P.live) atomicSub(P.live, 1);
+            }
+        }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
+    k2_body(a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,13 +248,13 @@ struct CubeSrc {
     // columns at a time in row order; every lane of a warp makes the same
     // number of calls (warp-collective work inside f is allowed).
     template <typename F>
-    __device__ void visit(F&& f) const {
+    __device__ void visit(const int bid, const int nblk, F&& f) const {
         const float cs = (float)(1.0 - sc->c[parity]);
         const unsigned quads = (unsigned)g.p2 / 4u;
         const unsigned n1 = (unsigned)g.n1;
         const unsigned total = (unsigned)nb * n1 * quads;       // < 2^31 for any cube that fits
         const unsigned row0 = (unsigned)o0 * n1;
-        for (unsigned base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+        for (unsigned base = bid * blockDim.x; base < total; base += nblk * blockDim.x) {
             const unsigned item = base + threadIdx.x;
             const bool live = item < total;
             const unsigned row = row0 + (live ? item / quads : 0u);   // b * n1 + i
@@ -268,8 +286,8 @@ struct FlatSrc {
     const float* x;
     long long n;
     template <typename F>
-    __device__ void visit(F&& f) const {
-        for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+    __device__ void visit(const int bid, const int nblk, F&& f) const {
+        for (long long base = bid * (long long)blockDim.x; base < n; base += (long long)nblk * blockDim.x) {
             const long long l = base + threadIdx.x;
             const bool valid = l < n;
             f(valid, valid ? fabsf(x[l]) : 0.f, 0.f);
@@ -282,13 +300,14 @@ struct SearchArgs {
     L1Work w;
     int nvec;        // 2 for the cube (s, t), 1 for a flat vector
     int cta_base = 0, cta_total = 0;   // this launch's CTAs among the stage's (0: alone)
-    __device__ int total() const { return cta_total > 0 ? cta_total : (int)gridDim.x; }
+    __device__ int total(int nblk) const { return cta_total > 0 ? cta_total : nblk; }
 };
 
 // Radix histogram pass of one level for every vector that needs it; the last
 // CTA selects the bracket.
 template <typename Src>
-__global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a, const int level) {
+__device__ __forceinline__ void radix_body(const Src& src, const SearchArgs& a, const int level, const int bid,
+                                           const int nblk) {
     extern __shared__ __align__(16) unsigned hsm[];   // [2][2048] counts, low and high residue halves
     __shared__ double sh_d[NT];
     __shared__ unsigned long long sh_u[NT];
@@ -322,7 +341,7 @@ __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a,
             }
         }
     };
-    src.visit([&](bool valid, float x0, float x1) {
+    src.visit(bid, nblk, [&](bool valid, float x0, float x1) {
         if (need[0]) {
             const unsigned key = __float_as_uint(x0);
             insert(0, valid && lv.inside(key, pre0), key);
@@ -341,7 +360,7 @@ __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a,
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->fb_ticket, 1u) == (unsigned)(a.total() - 1));
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.sc->fb_ticket, 1u) == (unsigned)(a.total(nblk) - 1));
     __syncthreads();
     if (!is_last) return;
     __threadfence();
@@ -352,6 +371,11 @@ __global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a,
     }
     for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) { a.w.hcnt[k] = 0; a.w.hres[k] = 0; }
     if (threadIdx.x == 0) a.sc->fb_ticket = 0;
+}
+
+template <typename Src>
+__global__ void __launch_bounds__(NT) k_radix(const Src src, const SearchArgs a, const int level) {
+    radix_body(src, a, level, blockIdx.x, gridDim.x);
 }
 
 // Candidates of one CTA collected in shared memory and appended to the global
@@ -403,7 +427,7 @@ struct BlockCand {
 // Gathers the bracket bin of every vector that needs it (k_search_finish
 // finishes tau).
 template <typename Src>
-__global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a) {
+__device__ __forceinline__ void gather_body(const Src& src, const SearchArgs& a, const int bid, const int nblk) {
     bool need[2];
     need[0] = a.sc->ctl[0].need == NEED_GATHER;
     need[1] = a.nvec > 1 && a.sc->ctl[1].need == NEED_GATHER;
@@ -411,11 +435,16 @@ __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a
     const float lo0 = a.sc->ctl[0].g_lo, hi0 = a.sc->ctl[0].g_hi;
     const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
     GSSTV_BLOCK_CAND(bc);
-    src.visit([&](bool valid, float x0, float x1) {
+    src.visit(bid, nblk, [&](bool valid, float x0, float x1) {
         if (need[0]) bc.append(0, valid && x0 > lo0 && x0 <= hi0, x0, a.w.cand[0], &a.sc->acc[0].m);
         if (need[1]) bc.append(1, valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
     });
     bc.flush(a.w.cand, a.sc);
+}
+
+template <typename Src>
+__global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a) {
+    gather_body(src, a, blockIdx.x, gridDim.x);
 }
 
 // One windowed pass after K1's window missed: count and sum of |x| above the
@@ -423,8 +452,8 @@ __global__ void __launch_bounds__(NT) k_gather(const Src src, const SearchArgs a
 // finish; a second miss leaves the threshold to the radix passes).  Per-CTA
 // partial sums go to pn / ps (the stencil pass's partial arrays, free by now).
 template <typename Src>
-__global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a, unsigned long long* pn,
-                                               double* ps) {
+__device__ __forceinline__ void window_body(const Src& src, const SearchArgs& a, unsigned long long* pn, double* ps,
+                                            const int bid, const int nblk) {
     __shared__ double red_d[64];
     __shared__ unsigned long long red_u[64];
     bool need[2];
@@ -435,7 +464,7 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
     const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
     WinAcc w0, w1;
     GSSTV_BLOCK_CAND(bc);
-    src.visit([&](bool valid, float x0, float x1) {
+    src.visit(bid, nblk, [&](bool valid, float x0, float x1) {
         if (need[0]) {
             const bool hi = valid && x0 > hi0;
             if (hi) { w0.n++; w0.s.add(x0); }
@@ -451,11 +480,17 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
     float2* pbuf = reinterpret_cast<float2*>(red_d);
     const unsigned long long n0 = block_sum(w0.n, red_u), n1 = block_sum(w1.n, red_u);
     const double s0 = block_sum_pair(w0.s, pbuf), s1 = block_sum_pair(w1.s, pbuf);
-    const int cta = a.cta_base + blockIdx.x;
+    const int cta = a.cta_base + bid;
     if (threadIdx.x == 0) {
         pn[2 * cta] = n0; pn[2 * cta + 1] = n1;
         ps[2 * cta] = s0; ps[2 * cta + 1] = s1;
     }
+}
+
+template <typename Src>
+__global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a, unsigned long long* pn,
+                                               double* ps) {
+    window_body(src, a, pn, ps, blockIdx.x, gridDim.x);
 }
 
 // The finish of the retry window (mode 0) or of the gathered radix bracket
@@ -469,9 +504,8 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
 constexpr int kFinishThreads = 1024;
 constexpr unsigned kFinishStage = 32768;
 constexpr size_t kFinishSmem = kFinishStage * sizeof(float) + 3 * kNarrowBins * sizeof(unsigned);
-__global__ void __launch_bounds__(kFinishThreads) k_search_finish(const SearchArgs a, int mode,
-                                                                   const unsigned long long* pn,
-                                                                   const double* ps, int parts) {
+__device__ __forceinline__ void finish_body(const SearchArgs& a, int mode, const unsigned long long* pn,
+                                            const double* ps, int parts) {
     extern __shared__ __align__(16) float fstage[];         // kFinishStage floats + the narrowing scratch
     __shared__ double red_d[64];
     __shared__ unsigned long long red_u[64];
@@ -523,6 +557,12 @@ __global__ void __launch_bounds__(kFinishThreads) k_search_finish(const SearchAr
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kFinishThreads) k_search_finish(const SearchArgs a, int mode,
+                                                                   const unsigned long long* pn,
+                                                                   const double* ps, int parts) {
+    finish_body(a, mode, pn, ps, parts);
 }
 
 // out = soft(x, tau) for the standalone projection
@@ -723,6 +763,90 @@ int launch_convert(const S* src, long long sp, long long sc_, D* dst, long long 
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+// ---------------------------------------------------------------------------
+// batches: one launch of a stage for many cubes (float32 storage)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_cube_of(const int* start, int n, int blk) {
+    int lo = 0, hi = n - 1;                 // the last cube whose first CTA is <= blk
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct SearchCube {
+    CubeSrc<float> src;
+    SearchArgs a;
+    unsigned long long* pn;
+    double* ps;
+    int parts;
+};
+struct SearchBatchTab {
+    int n;
+    int start[kBatchMax + 1];
+    SearchCube c[kBatchMax];
+};
+struct K2BatchTab {
+    int n;
+    int start[kBatchMax + 1];
+    K2Args<float> c[kBatchMax];
+};
+
+__global__ void __launch_bounds__(NT) k_window_batch(const __grid_constant__ SearchBatchTab t) {
+    const int c = batch_cube_of(t.start, t.n, blockIdx.x);
+    const SearchCube& q = t.c[c];
+    if (__ldcg(&q.a.sc->done)) return;
+    window_body(q.src, q.a, q.pn, q.ps, blockIdx.x - t.start[c], t.start[c + 1] - t.start[c]);
+}
+__global__ void __launch_bounds__(NT) k_radix_batch(const __grid_constant__ SearchBatchTab t, const int level) {
+    const int c = batch_cube_of(t.start, t.n, blockIdx.x);
+    const SearchCube& q = t.c[c];
+    if (__ldcg(&q.a.sc->done)) return;
+    radix_body(q.src, q.a, level, blockIdx.x - t.start[c], t.start[c + 1] - t.start[c]);
+}
+__global__ void __launch_bounds__(NT) k_gather_batch(const __grid_constant__ SearchBatchTab t) {
+    const int c = batch_cube_of(t.start, t.n, blockIdx.x);
+    const SearchCube& q = t.c[c];
+    if (__ldcg(&q.a.sc->done)) return;
+    gather_body(q.src, q.a, blockIdx.x - t.start[c], t.start[c + 1] - t.start[c]);
+}
+// one CTA per cube
+__global__ void __launch_bounds__(kFinishThreads) k_finish_batch(const __grid_constant__ SearchBatchTab t,
+                                                                  const int mode) {
+    const SearchCube& q = t.c[blockIdx.x];
+    if (__ldcg(&q.a.sc->done)) return;
+    finish_body(q.a, mode, q.pn, q.ps, q.parts);
+}
+__global__ void __launch_bounds__(NT) k2_batch(const __grid_constant__ K2BatchTab t) {
+    const int c = batch_cube_of(t.start, t.n, blockIdx.x);
+    const K2Args<float>& a = t.c[c];
+    if (__ldcg(&a.sc->done)) return;
+    k2_body(a, blockIdx.x - t.start[c], t.start[c + 1] - t.start[c]);
+}
+
+// the search table of a stage; grid(q): CTAs of cube q's share
+template <typename G>
+int search_table(const BatchCube* cubes, int n, SearchBatchTab& t, G&& grid) {
+    if (n < 1 || n > kBatchMax) return -1;
+    static_assert(sizeof(SearchBatchTab) <= 32000, "kernel parameter space");
+    t.n = n;
+    int total = 0;
+    for (int c = 0; c < n; ++c) {
+        const BatchCube& q = cubes[c];
+        const SlabPart whole = whole_cube(q.g);
+        t.c[c].src = make_cube_src<float>(q.g, q.b, q.p, q.sc, whole);
+        t.c[c].a = cube_args(q.sc, q.l1, whole);
+        t.c[c].pn = q.l1.k1_n;
+        t.c[c].ps = q.l1.k1_s;
+        t.c[c].parts = window_grid_n(part_voxels(q.g, whole), q.k1_ctas);
+        t.start[c] = total;
+        total += grid(q, whole);
+    }
+    t.start[n] = total;
+    return total;
+}
+
 }  // namespace
 
 int device_sms() {
@@ -816,6 +940,79 @@ int launch_window(int storage, const Geom& g, const IterBufs& b, const IterParam
         case 2: return launch_window_t<__half>(g, b, p, sc, w, part_cap, sp, st);
     }
     return -1;
+}
+
+int launch_window_batch(const BatchCube* cubes, int n, cudaStream_t st) {
+    SearchBatchTab t{};
+    const int total = search_table(cubes, n, t, [](const BatchCube& q, const SlabPart& w) {
+        return window_grid_n(part_voxels(q.g, w), q.k1_ctas);
+    });
+    if (total < 0) return -1;
+    k_window_batch<<<total, NT, 0, st>>>(t);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_radix_batch(const BatchCube* cubes, int n, int level, cudaStream_t st) {
+    SearchBatchTab t{};
+    const int total = search_table(cubes, n, t, [](const BatchCube& q, const SlabPart& w) {
+        return radix_grid_n(part_voxels(q.g, w));
+    });
+    if (total < 0) return -1;
+    k_radix_batch<<<total, NT, 6 * kHistBins * sizeof(unsigned), st>>>(t, level);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_gather_batch(const BatchCube* cubes, int n, cudaStream_t st) {
+    SearchBatchTab t{};
+    const int total = search_table(cubes, n, t, [](const BatchCube& q, const SlabPart& w) {
+        return gather_grid_n(part_voxels(q.g, w));
+    });
+    if (total < 0) return -1;
+    k_gather_batch<<<total, NT, 0, st>>>(t);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st) {
+    SearchBatchTab t{};
+    if (search_table(cubes, n, t, [](const BatchCube&, const SlabPart&) { return 1; }) < 0) return -1;
+    k_finish_batch<<<n, kFinishThreads, kFinishSmem, st>>>(t, mode);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_k2_batch(const BatchCube* cubes, int n, cudaStream_t st) {
+    if (n < 1 || n > kBatchMax) return -1;
+    static_assert(sizeof(K2BatchTab) <= 32000, "kernel parameter space");
+    K2BatchTab t{};
+    t.n = n;
+    int total = 0;
+    for (int c = 0; c < n; ++c) {
+        const BatchCube& q = cubes[c];
+        K2Args<float>& a = t.c[c];
+        a.g = q.g;
+        a.u = (const float*)q.b.u; a.u_n = (const float*)q.b.u_n; a.s = (const float*)q.b.s;
+        a.t = (const float*)q.b.t; a.y3 = (const float*)q.b.y3; a.q = (const float*)q.b.q; a.v = q.b.v;
+        a.s_n = (float*)q.b.s_n; a.t_n = (float*)q.b.t_n; a.y3_n = (float*)q.b.y3_n; a.q_n = (float*)q.b.q_n;
+        a.p = q.p;
+        a.sc = q.sc;
+        a.part = q.k2_part;
+        a.sp = whole_cube(q.g);
+        t.start[c] = total;
+        total += std::min(k2_grid_part(q.g, a.sp), q.k2_cap);
+    }
+    t.start[n] = total;
+    k2_batch<<<total, NT, 0, st>>>(t);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int k1_batch_configure();
+
+int batch_configure() {
+    if (k1_batch_configure() != 0) return -3;
+    cudaError_t e = cudaFuncSetAttribute(k_radix_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(6 * kHistBins * sizeof(unsigned)));
+    if (e != cudaSuccess) return -3;
+    e = cudaFuncSetAttribute(k_finish_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFinishSmem);
+    return e == cudaSuccess ? 0 : -3;
 }
 
 int launch_copy_f32(const float* src, long long src_pitch, long long src_cube, float* dst, long long dst_pitch,

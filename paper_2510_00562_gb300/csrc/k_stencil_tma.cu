@@ -559,7 +559,10 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     return true;
 }
 
-__global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps maps, const K1TArgs a) {
+// One CTA of K1: the tile (bx, by) and band run bz of a launch of gx x gy x gz
+// CTAs over one cube (a launch of its own, or the cube's share of a batch).
+__device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, const int bx, const int by,
+                                       const int bz, const int gx, const int gy, const int gz) {
     using L = Lay;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ double red_d[64];
@@ -568,8 +571,8 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     __shared__ int is_last, sh_flag;
     const Geom& g = a.g;
     const IterParams& P = a.p;
-    const int i0 = blockIdx.y * L::TY, j0 = blockIdx.x * L::TX;
-    const int b0 = a.sp.o0 + blockIdx.z * a.chunk;
+    const int i0 = by * L::TY, j0 = bx * L::TX;
+    const int b0 = a.sp.o0 + bz * a.chunk;
     const int b1 = min(a.sp.o1, b0 + a.chunk);
     const int tid = threadIdx.x;
     const float cs = (float)(1.0 - a.sc->c[P.parity]);
@@ -621,8 +624,8 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     }
 
     // this CTA among every CTA of the pass stage (all slabs of a split cube)
-    const int cta = a.sp.cta_base + blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const int ncta = a.sp.cta_total > 0 ? a.sp.cta_total : (int)(gridDim.x * gridDim.y * gridDim.z);
+    const int cta = a.sp.cta_base + bx + gx * (by + gy * bz);
+    const int ncta = a.sp.cta_total > 0 ? a.sp.cta_total : gx * gy * gz;
     if (W.s || W.t) {
         // the buffered window candidates join the global list (one atomic per vector)
         __syncthreads();
@@ -776,6 +779,39 @@ __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps 
     if (tid == 0) a.sc->k1_ticket = 0;
 }
 
+__global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps maps, const K1TArgs a) {
+    k1_run(maps, a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z);
+}
+
+// K1 over many cubes in one launch: the cube of a CTA from a table of first
+// CTAs, its arguments from the table, its tensor maps from device memory.
+struct K1BatchTab {
+    int n;
+    int start[kBatchMax + 1];
+    short gx[kBatchMax], gy[kBatchMax], gz[kBatchMax];
+    const K1Maps* maps[kBatchMax];
+    K1TArgs args[kBatchMax];
+};
+
+__device__ __forceinline__ int batch_cube_of(const int* start, int n, int blk) {
+    int lo = 0, hi = n - 1;                 // the last cube whose first CTA is <= blk
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(512, 1) k1_tma_batch(const __grid_constant__ K1BatchTab t) {
+    const int c = batch_cube_of(t.start, t.n, blockIdx.x);
+    const K1TArgs& a = t.args[c];
+    if (__ldcg(&a.sc->done)) return;        // this cube has stopped
+    const int gx = t.gx[c], gy = t.gy[c], gz = t.gz[c];
+    const int l = blockIdx.x - t.start[c];
+    const int bx = l % gx, by = (l / gx) % gy, bz = l / (gx * gy);
+    k1_run(*t.maps[c], a, bx, by, bz, gx, gy, gz);
+}
+
 // Bands per CTA.  One CTA runs per SM, so a launch of U CTAs on S SMs takes
 // ceil(U / S) waves and the last wave leaves SMs idle; every CTA also pays a
 // prologue of about 1.5 band steps (its first copies, D^T y2 of the band
@@ -878,6 +914,43 @@ int k1_tma_grid(const Geom& g, const SlabPart& sp, int chunk) {
     const int tx = (g.n2 + Lay::TX - 1) / Lay::TX, ty = (g.n1 + Lay::TY - 1) / Lay::TY;
     const int c = part_chunk(g, nb, chunk);
     return tx * ty * ((nb + c - 1) / c);
+}
+
+int launch_k1_batch(const BatchCube* cubes, int n, cudaStream_t st) {
+    if (n < 1 || n > kBatchMax) return -1;
+    static_assert(sizeof(K1BatchTab) <= 32000, "kernel parameter space");
+    K1BatchTab t{};
+    t.n = n;
+    int total = 0;
+    for (int c = 0; c < n; ++c) {
+        const BatchCube& q = cubes[c];
+        const SlabPart whole = whole_cube(q.g);
+        K1TArgs& a = t.args[c];
+        a.g = q.g;
+        a.u_n = (float*)q.b.u_n; a.w1_n = (float*)q.b.w1_n; a.w2_n = (float*)q.b.w2_n;
+        a.y1_n = (float*)q.b.y1_n; a.y2_n = (float*)q.b.y2_n;
+        a.p = q.p;
+        a.sc = q.sc;
+        a.l1 = q.l1;
+        a.sp = whole;
+        a.chunk = part_chunk(q.g, q.g.n3, q.k1_chunk);
+        a.hist_fits = a.chunk * Lay::NT <= 65535;
+        const int tx = (q.g.n2 + Lay::TX - 1) / Lay::TX, ty = (q.g.n1 + Lay::TY - 1) / Lay::TY;
+        const int tz = (q.g.n3 + a.chunk - 1) / a.chunk;
+        if (tx > 32767 || ty > 32767 || tz > 32767) return -1;
+        t.gx[c] = (short)tx; t.gy[c] = (short)ty; t.gz[c] = (short)tz;
+        t.maps[c] = q.maps;
+        t.start[c] = total;
+        total += tx * ty * tz;
+    }
+    t.start[n] = total;
+    k1_tma_batch<<<total, Lay::NT, Lay::SMEM, st>>>(t);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int k1_batch_configure() {
+    const cudaError_t e = cudaFuncSetAttribute(k1_tma_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM);
+    return e == cudaSuccess ? 0 : -3;
 }
 
 int launch_k1_tma(int storage, const Geom& g, const K1Maps& m, const IterBufs& b, const IterParams& p,

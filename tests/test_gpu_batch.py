@@ -99,3 +99,34 @@ def test_batch_rejects_mismatched_inputs():
             bt.solve([torch.zeros(3, 8, 9, device="cuda")])
         with pytest.raises(ValueError):
             bt.solve([])
+
+
+def test_fused_batch_equals_stream_batch_and_single_solves(monkeypatch):
+    """Float32 cubes run each stage as one launch over all cubes, with the
+    stopping rules on the device: every cube must stop at the pass its single
+    solve stops at, with the same result; the one-stream-per-cube batch
+    (GSSTV_BATCH=streams) too."""
+    cases = [c for c in CASES if c[2].get("storage", "fp32") == "fp32"]
+    pbs = [_cube(*shape, seed=10 + k, sigma=n[0], sp=n[1], st=n[2]) for k, (shape, n, _) in enumerate(cases)]
+    params = [_params(pb, kw) for pb, (_, _, kw) in zip(pbs, cases)]
+    vs = [torch.from_numpy(pb["v"]).cuda() for pb in pbs]
+    shapes = [c[0] for c in cases]
+    with GeoSSTVBatch(shapes, params) as bt:
+        us, ss, ts, done = bt.solve(vs)
+        us2, _, _, done2 = bt.solve(vs)                 # a second solve repeats the first
+        stats = [bt.stats(k) for k in range(len(cases))]
+    monkeypatch.setenv("GSSTV_BATCH", "streams")
+    with GeoSSTVBatch(shapes, params) as bs:
+        us_s, _, _, done_s = bs.solve(vs)
+    assert done == done2 == done_s
+    for k, ((n1, n2, n3), _, kw) in enumerate(cases):
+        with GeoSSTVSolver(n1, n2, n3, _params(pbs[k], kw)) as sol:
+            u, s, t, n = sol.solve(vs[k])
+        assert done[k] == n, (k, done[k], n)
+        for got, ref in ((us[k], u), (ss[k], s), (ts[k], t), (us2[k], u), (us_s[k], u)):
+            e = rel(got.cpu().numpy(), ref.cpu().numpy())
+            assert e < 1e-6 or not ref.any(), (k, e)
+        assert stats[k]["iterations"] >= n
+    early = [(done[k], kw["max_iter"]) for k, (_, _, kw) in enumerate(cases) if kw.get("tol", 0.0) > 0]
+    assert any(d < cap for d, cap in early)
+
