@@ -643,6 +643,51 @@ def run_omega_sweep(args):
     return 0
 
 
+def run_slabs(args):
+    """The bench cube stored as S band slabs on this one GPU (gsstv_slabs_*):
+    every kernel once per slab, the slabs' sums finished together, halo
+    planes copied after each pass; against the single handle on the same
+    passes.  One JSON line (the cost of the split on one device: extra
+    launches, halo copies, and each slab's halo bands)."""
+    import numpy as np
+    import torch
+    from paper_2510_00562_gb300 import build, synth
+    from paper_2510_00562_gb300.solver import GeoSSTVSlabs, GeoSSTVSolver, make_params
+    build.build()
+    n1, n2, n3 = args.shape
+    nvox = n1 * n2 * n3
+    pb = synth.make_problem(n1, n2, n3, seed=0, noise=synth.NoiseSpec(**NOISE))
+    p = make_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03, max_iter=args.steps,
+                    graph_iters=16)
+    v = torch.from_numpy(pb["v"]).cuda()
+    out = {"slabs": {"workload": WORKLOAD if args.shape == SHAPE else f"{n1}x{n2}x{n3} cube", "steps": args.steps,
+                     "warmup": args.warmup, "unit": UNIT}}
+
+    def timed(obj):
+        obj.load(v)
+        obj.iterate(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        obj.iterate(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    with GeoSSTVSolver(n1, n2, n3, p) as sol:
+        ms = timed(sol)
+        u_ref = sol.get_state()["u"]
+    out["slabs"]["single"] = {"ms_per_step": ms / args.steps, "value": nvox * args.steps / (ms * 1e-3)}
+    for S in args.slabs:
+        with GeoSSTVSlabs(n1, n2, n3, S, p) as sl:
+            ms = timed(sl)
+            du = float((sl.get_state()["u"] - u_ref).abs().max().item())
+        out["slabs"][str(S)] = {"ms_per_step": ms / args.steps, "value": nvox * args.steps / (ms * 1e-3),
+                                "max_abs_u_diff_vs_single": du}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_precision_study(args):
     """The precision form on a cube of its own (default 1024x1024x200, 5000
     iterations: 4000 16-bit + 1000 FP32 against 5000 FP32), one JSON line."""
@@ -866,6 +911,8 @@ def main(argv=None):
                     help="run only the reverse-mode measurement on a cube of this size")
     ap.add_argument("--grad-iters", type=int, default=200)
     ap.add_argument("--grad-ckpt", type=int, default=20, help="passes between checkpoints")
+    ap.add_argument("--slabs", type=int, nargs="*", default=None, metavar="S",
+                    help="run only the band-slab measurement with these slab counts")
     ap.add_argument("--shape", default="512x512x224",
                     help="N1xN2xN3; anything but the default is a profiling case, not a bench line")
     args = ap.parse_args(argv)
@@ -874,6 +921,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.slabs:
+        return run_slabs(args)
     if args.precision_study:
         return run_precision_study(args)
     if args.batch:
