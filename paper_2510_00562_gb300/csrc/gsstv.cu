@@ -329,6 +329,8 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.k1_n, 4 * (size_t)h->k1_ctas * sizeof(unsigned long long));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.k1_s, 4 * (size_t)h->k1_ctas * sizeof(double));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.khist, 2 * (size_t)kK1Bins * sizeof(unsigned));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.nh, 2 * 3 * (size_t)kNarrowBins * sizeof(unsigned));
+    if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->l1.nbinned, 2 * sizeof(unsigned));
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->k2_part, 3 * (size_t)h->k2_cap * sizeof(double));
     if (rc == GSSTV_OK) {
         h->ev.resize(512);
@@ -769,6 +771,7 @@ struct gsstv_batch {
     cudaGraphExec_t gexec = nullptr;
     int graph_len = 0;
     std::vector<int> graph_chunks;  // the cubes' K1 band runs the graph was built with
+    std::vector<int> graph_set;     // and the cubes it runs
 };
 
 int gsstv_batch_destroy(gsstv_batch* b) {
@@ -854,13 +857,15 @@ int gsstv_batch_size(const gsstv_batch* b) { return b ? (int)b->h.size() : 0; }
 
 namespace {
 
-// One pass of every unfinished cube from parity `par`: each stage one launch.
-int batch_enqueue(gsstv_batch* b, int par, cudaStream_t st) {
-    const int nc = (int)b->h.size();
+// One pass of the cubes in `set` from parity `par`: each stage one launch
+// (a cube that has stopped returns at once from each).
+int batch_enqueue(gsstv_batch* b, const std::vector<int>& set, int par, cudaStream_t st) {
+    const int nc = (int)set.size();
     BatchCube cubes[kBatchMax];
-    for (int c = 0; c < nc; ++c) {
+    for (int k = 0; k < nc; ++k) {
+        const int c = set[k];
         gsstv_handle* h = b->h[c];
-        BatchCube& q = cubes[c];
+        BatchCube& q = cubes[k];
         q.g = h->g;
         q.b = bufs(h, par);
         q.p = iparams(h, par);
@@ -886,15 +891,41 @@ int batch_enqueue(gsstv_batch* b, int par, cudaStream_t st) {
     return GSSTV_OK;
 }
 
+// The graph of G passes over the cubes in `set` (rebuilt only when the set
+// or a cube's K1 band run has changed).
+int batch_graph(gsstv_batch* b, const std::vector<int>& set, int G) {
+    std::vector<int> chunks;
+    for (int c : set) chunks.push_back(b->h[c]->k1_chunk);   // (the autotuner may change them)
+    if (b->gexec && b->graph_len == G && chunks == b->graph_chunks && set == b->graph_set) return GSSTV_OK;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    TRY(cuda_rc(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)));
+    int rc = GSSTV_OK;
+    for (int k = 0; k < G && rc == GSSTV_OK; ++k) rc = batch_enqueue(b, set, k & 1, b->cap);
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc != GSSTV_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    TRY(cuda_rc(e));
+    const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    TRY(cuda_rc(ei));
+    b->graph_len = G;
+    b->graph_chunks = chunks;
+    b->graph_set = set;
+    return GSSTV_OK;
+}
+
 // The fused solve: every cube from its standard start, blocks of passes as
 // one CUDA graph (even length: the parity comes back to 0) until no cube is
 // left iterating.  A cube stops on the device at the pass its own stopping
 // rule names, exactly as gsstv_iterate stops it (Eq. 28 every check_every
-// passes, or max_iter).
+// passes, or max_iter).  After a block in which cubes stopped, the graph is
+// rebuilt over the cubes still iterating, so that stopped cubes stop costing
+// launches; they all sit at parity 0 then, having run every pass so far.
 int batch_solve_fused(gsstv_batch* b, const float* const* d_v, float* const* d_u, float* const* d_s,
                       float* const* d_t, int* iters_done) {
     const int nc = (int)b->h.size();
     int live = 0, most = 0;
+    std::vector<int> set;
     for (int c = 0; c < nc; ++c) {
         gsstv_handle* h = b->h[c];
         TRY(gsstv_load_observation(h, d_v[c]));
@@ -902,6 +933,7 @@ int batch_solve_fused(gsstv_batch* b, const float* const* d_v, float* const* d_u
         if (h->p.max_iter > 0) {
             ++live;
             most = std::max(most, h->p.max_iter);
+            set.push_back(c);
         } else {                                         // nothing to run: stopped at the start
             const int one[2] = {1, 0};
             TRY(cuda_rc(cudaMemcpy(&h->sc->done, one, sizeof(one), cudaMemcpyHostToDevice)));
@@ -909,24 +941,20 @@ int batch_solve_fused(gsstv_batch* b, const float* const* d_v, float* const* d_u
     }
     TRY(cuda_rc(cudaMemcpyAsync(b->live, &live, sizeof(int), cudaMemcpyHostToDevice, b->caller)));
     const int G = 16;
-    std::vector<int> chunks(nc);
-    for (int c = 0; c < nc; ++c) chunks[c] = b->h[c]->k1_chunk;   // (the autotuner may change them)
-    if (!b->gexec || b->graph_len != G || chunks != b->graph_chunks) {
-        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
-        cudaGraph_t graph = nullptr;
-        TRY(cuda_rc(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)));
-        int rc = GSSTV_OK;
-        for (int k = 0; k < G && rc == GSSTV_OK; ++k) rc = batch_enqueue(b, k & 1, b->cap);
-        const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
-        if (rc != GSSTV_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
-        TRY(cuda_rc(e));
-        const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
-        cudaGraphDestroy(graph);
-        TRY(cuda_rc(ei));
-        b->graph_len = G;
-        b->graph_chunks = chunks;
-    }
     for (int run = 0; live > 0 && run < most; run += G) {
+        if (live < (int)set.size()) {
+            // which cubes stopped in the last block (their done flags)
+            for (int c : set)
+                TRY(cuda_rc(cudaMemcpyAsync(&b->pinned[c].done, &b->h[c]->sc->done, sizeof(int),
+                                            cudaMemcpyDeviceToHost, b->caller)));
+            TRY(cuda_rc(cudaStreamSynchronize(b->caller)));
+            std::vector<int> keep;
+            for (int c : set)
+                if (!b->pinned[c].done) keep.push_back(c);
+            set.swap(keep);
+            if (set.empty()) break;
+        }
+        TRY(batch_graph(b, set, G));
         TRY(cuda_rc(cudaGraphLaunch(b->gexec, b->caller)));
         TRY(cuda_rc(cudaMemcpyAsync(b->live_host, b->live, sizeof(int), cudaMemcpyDeviceToHost, b->caller)));
         TRY(cuda_rc(cudaStreamSynchronize(b->caller)));
@@ -1291,6 +1319,8 @@ int gsstv_slabs_create(gsstv_slabs** out, int n1, int n2, int n3, int nslabs, co
         if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.k1_n, part_n * sizeof(unsigned long long));
         if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.k1_s, part_n * sizeof(double));
         if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.khist, 2 * (size_t)kK1Bins * sizeof(unsigned));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.nh, 2 * 3 * (size_t)kNarrowBins * sizeof(unsigned));
+        if (rc == GSSTV_OK) rc = slabs_alloc(G, (void**)&G->l1.nbinned, 2 * sizeof(unsigned));
         if (rc == GSSTV_OK)
             rc = slabs_alloc(G, (void**)&G->k2_part, 3 * (size_t)G->k2p[0].cta_total * sizeof(double));
     }

@@ -162,6 +162,7 @@ struct Scal {
 
 constexpr int kHistBins = 2048;        // radix histogram bins per vector
 constexpr unsigned kCandCap = 1u << 20; // candidate capacity per vector
+constexpr int kNarrowBins = 2048;        // bins of one narrowing round of a candidate list
 constexpr double kCandTarget = 65536.0;  // K1's window is sized for at most about this many candidates
 constexpr double kRetryTarget = 262144.0; // a retry window after a miss: at most about this many
 constexpr unsigned kGatherMax = 1u << 16; // a radix bracket this small is gathered, a larger one refined
@@ -183,6 +184,11 @@ struct L1Work {
     unsigned long long* k1_n;          // per K1 CTA: [4] counts (window s, t; histogram top s, t)
     double* k1_s;                      // per K1 CTA: [4] sums
     unsigned* khist;                   // [2][kK1Bins] K1 histogram counts (zero between passes)
+    // key histogram of each candidate list ([2][3 kNarrowBins]: bin counts, low and
+    // high 10 bits of the key residues), filled by the passes that append the
+    // candidates and cleared by the finish that reads it; null: not kept
+    unsigned* nh;
+    unsigned* nbinned;                 // [2] candidates counted into nh
 };
 
 // ---------------------------------------------------------------------------

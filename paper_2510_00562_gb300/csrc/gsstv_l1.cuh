@@ -67,13 +67,61 @@ __device__ __forceinline__ void for_each_candidate(const float* cand, unsigned m
 // phi >= 0 brackets the root; the bins above it join the "above" count and
 // sum.  Repeated on that bin until it holds at most kNarrowStage values,
 // which are then staged in the scratch for Michelot's step.
-constexpr int kNarrowBins = 2048;
 constexpr unsigned kNarrowStage = 3 * kNarrowBins;   // floats the scratch stages
 constexpr unsigned kNarrowMin = 4096;                // candidates beyond this are narrowed first
 
+// Bin geometry of one narrowing round over the key window (klo, khi]: bins of
+// 2^shift keys counted from base = klo >> shift, nb of them, with the
+// smallest shift that needs at most kNarrowBins bins.  ok: the window spans
+// at most 16 binary orders (then nb <= kNarrowBins and the integer sums of
+// the bins are exact).
+struct NarrowGeom {
+    unsigned base;
+    int shift, nb;
+    bool ok;
+};
+__device__ __forceinline__ NarrowGeom narrow_geom(unsigned klo, unsigned khi) {
+    NarrowGeom g;
+    g.shift = 0;
+    while (g.shift < 20 && ((khi >> g.shift) - (klo >> g.shift)) >= (unsigned)kNarrowBins) ++g.shift;
+    g.base = klo >> g.shift;
+    g.nb = (int)((khi >> g.shift) - g.base) + 1;
+    g.ok = max((int)((khi >> 23) & 0xffu), 1) - max((int)(((klo + 1u) >> 23) & 0xffu), 1) <= 16;
+    return g;
+}
+// Counts a key of the window into a narrowing histogram h: kNarrowBins bin
+// counts, then the sums of the low and of the high 10 bits of the keys'
+// residues below the bin edge (shared or global memory).
+__device__ __forceinline__ void narrow_add(unsigned* h, const NarrowGeom& g, unsigned key) {
+    const int b = (int)((key >> g.shift) - g.base);
+    const unsigned res = key - ((key >> g.shift) << g.shift);
+    atomicAdd(h + b, 1u);
+    if (res) {
+        atomicAdd(h + kNarrowBins + b, res & 1023u);
+        atomicAdd(h + 2 * kNarrowBins + b, res >> 10);
+    }
+}
+// The key histogram of vector v's candidate list when every one of its m
+// candidates was counted into it (built by the passes that appended them,
+// over the same window), else null.
+__device__ __forceinline__ const unsigned* narrow_pre(const L1Work& w, int v, unsigned m) {
+    return (w.nh && m > 0u && __ldcg(w.nbinned + v) == m) ? w.nh + v * 3 * kNarrowBins : nullptr;
+}
+// Clears vector v's list histogram after its finish has read it (whole block).
+__device__ __forceinline__ void narrow_clear(const L1Work& w, int v) {
+    if (!w.nh) return;
+    const unsigned used = __ldcg(w.nbinned + v);
+    __syncthreads();
+    if (used == 0u) return;
+    for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) w.nh[v * 3 * kNarrowBins + k] = 0u;
+    if (threadIdx.x == 0) w.nbinned[v] = 0u;
+}
+
 // Whole block.  cand[0..m): the candidates, every one in (klo, khi] as keys;
 // scr: 3 kNarrowBins unsigned of shared memory; sh_d: 4 doubles, wtot: 64
-// unsigned long long of shared memory.  On
+// unsigned long long of shared memory; pre (optional): the candidates' key
+// histogram over (klo, khi], already built (the first round reads it instead
+// of binning the candidates).  On
 // return 0: (klo, khi] narrowed, n_hi / s_hi now count everything above khi,
 // and the *m_st values in the new window are staged as floats in scr.
 // Returns 1 when phi at the window's lower end is negative (the root lies
@@ -82,7 +130,7 @@ constexpr unsigned kNarrowMin = 4096;                // candidates beyond this a
 // narrow in a few rounds.
 static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m, double& n_hi, double& s_hi,
                                 unsigned& klo, unsigned& khi, double r, unsigned* scr, unsigned* m_st, int* sh_i,
-                                double* sh_d, unsigned long long* wtot) {
+                                double* sh_d, unsigned long long* wtot, const unsigned* pre = nullptr) {
     // every candidate, from global memory (batched loads) or from shared memory
     auto each = [&](auto&& f) {
         if (cand_shared) {
@@ -95,27 +143,23 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
     unsigned* rlo = scr + kNarrowBins;
     unsigned* rhi = scr + 2 * kNarrowBins;
     for (int round = 0; round < 8; ++round) {
-        int shift = 0;
-        while (shift < 20 && ((khi >> shift) - (klo >> shift)) >= (unsigned)kNarrowBins) ++shift;
-        const unsigned base = klo >> shift;
-        const int nb = (int)((khi >> shift) - base) + 1;
+        const NarrowGeom ng = narrow_geom(klo, khi);
+        const int shift = ng.shift;
+        const unsigned base = ng.base;
+        const int nb = ng.nb;
         // the integer sums below need a window of at most 16 binary orders
-        if (max((int)((khi >> 23) & 0xffu), 1) - max((int)(((klo + 1u) >> 23) & 0xffu), 1) > 16) return 2;
+        if (!ng.ok) return 2;
         __syncthreads();
-        for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) scr[k] = 0u;
-        __syncthreads();
-        each([&](float x, unsigned) {
-            const unsigned key = __float_as_uint(x);
-            if (key > klo && key <= khi) {
-                const int b = (int)((key >> shift) - base);
-                const unsigned res = key - ((key >> shift) << shift);
-                atomicAdd(cnt + b, 1u);
-                if (res) {
-                    atomicAdd(rlo + b, res & 1023u);
-                    atomicAdd(rhi + b, res >> 10);
-                }
-            }
-        });
+        if (round == 0 && pre) {
+            for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) scr[k] = __ldcg(pre + k);
+        } else {
+            for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) scr[k] = 0u;
+            __syncthreads();
+            each([&](float x, unsigned) {
+                const unsigned key = __float_as_uint(x);
+                if (key > klo && key <= khi) narrow_add(scr, ng, key);
+            });
+        }
         __syncthreads();
         // Exact sums in units of u0, the ulp at the window's lowest key: every
         // float in the window is an integer multiple of u0 (below 2^40 of
@@ -234,13 +278,16 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
 // kNarrowMin candidates the window is first narrowed on the float keys
 // (l1_narrow; from the stage when they fit it, else from global memory), so
 // that Michelot's passes run over the few values of one narrow bin instead
-// of every candidate.
+// of every candidate.  pre (optional): the candidates' key histogram over the
+// window, built while they were appended; the first narrowing round then
+// reads it, and only the values of the chosen bin are staged (one pass over
+// the list).
 static __device__ int l1_window_finish(double n_hi, double s_hi, const float* cand, unsigned m_raw,
                                        double theta_lo, double theta_hi, double r,
                                        double* tau_out, double* red_d,
                                        unsigned long long* red_u, WinInfo* info = nullptr,
                                        float* stage = nullptr, unsigned stage_cap = 0,
-                                       unsigned* scr = nullptr) {
+                                       unsigned* scr = nullptr, const unsigned* pre = nullptr) {
     const double phi_hi = s_hi - n_hi * theta_hi - r;
     if (info) info->phi_hi = phi_hi;
     if (m_raw > kCandCap) return 1;
@@ -251,6 +298,8 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
         unsigned klo = __float_as_uint((float)theta_lo), khi = __float_as_uint((float)theta_hi);
         if ((double)__uint_as_float(klo) > theta_lo) klo -= 1u;        // rounding of the ends
         if ((double)__uint_as_float(khi) < theta_hi) khi += 1u;
+        // a key histogram built over the float window fits only that window
+        if ((double)(float)theta_lo != theta_lo || (double)(float)theta_hi != theta_hi) pre = nullptr;
         unsigned m_st = 0;
         __shared__ int nr_i[1];
         double nh = n_hi, sh = s_hi;
@@ -258,14 +307,14 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
         // memory once and narrowed from shared memory
         const float* src = cand;
         bool src_shared = false;
-        if (stage && m <= stage_cap) {
+        if (stage && m <= stage_cap && !pre) {
             for_each_candidate(cand, m, [&](float x, unsigned k) { stage[k] = x; });
             __syncthreads();
             src = stage;
             src_shared = true;
         }
         // (red_d and red_u serve as the narrowing's scalars and warp totals)
-        const int rc = l1_narrow(src, src_shared, m, nh, sh, klo, khi, r, scr, &m_st, nr_i, red_d, red_u);
+        const int rc = l1_narrow(src, src_shared, m, nh, sh, klo, khi, r, scr, &m_st, nr_i, red_d, red_u, pre);
         if (rc == 1) {
             // phi(theta_lo) < 0: as below, inside the ball or a miss below
             if (info) { info->phi_lo = red_d[2]; info->n_lo = red_d[3]; }

@@ -417,6 +417,18 @@ struct BlockCand {
                 if (base[v] + k < kCandCap) gcand[v][base[v] + k] = buf[v][k];
         }
     }
+    // after flush: counts the buffered candidates of vector v, all in the key
+    // window (lo, hi], into the list's key histogram (a candidate that
+    // overflowed the buffer is not counted, so the finish does without it)
+    __device__ void bin(const L1Work& w, int v, float lo, float hi) {
+        if (!w.nh) return;
+        const NarrowGeom ng = narrow_geom(__float_as_uint(lo), __float_as_uint(hi));
+        if (!ng.ok) return;
+        const unsigned n = min(cnt[v], (unsigned)kBlkCand);
+        unsigned* h = w.nh + v * 3 * kNarrowBins;
+        for (unsigned k = threadIdx.x; k < n; k += blockDim.x) narrow_add(h, ng, __float_as_uint(buf[v][k]));
+        if (threadIdx.x == 0 && n) atomicAdd(w.nbinned + v, n);
+    }
 };
 #define GSSTV_BLOCK_CAND(name)                                   \
     __shared__ float name##_buf[2][kBlkCand];                    \
@@ -440,6 +452,8 @@ __device__ __forceinline__ void gather_body(const Src& src, const SearchArgs& a,
         if (need[1]) bc.append(1, valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
     });
     bc.flush(a.w.cand, a.sc);
+    if (need[0]) bc.bin(a.w, 0, lo0, hi0);
+    if (need[1]) bc.bin(a.w, 1, lo1, hi1);
 }
 
 template <typename Src>
@@ -477,6 +491,8 @@ __device__ __forceinline__ void window_body(const Src& src, const SearchArgs& a,
         }
     });
     bc.flush(a.w.cand, a.sc);
+    if (need[0]) bc.bin(a.w, 0, lo0, hi0);
+    if (need[1]) bc.bin(a.w, 1, lo1, hi1);
     float2* pbuf = reinterpret_cast<float2*>(red_d);
     const unsigned long long n0 = block_sum(w0.n, red_u), n1 = block_sum(w1.n, red_u);
     const double s0 = block_sum_pair(w0.s, pbuf), s1 = block_sum_pair(w1.s, pbuf);
@@ -494,26 +510,28 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
 }
 
 // The finish of the retry window (mode 0) or of the gathered radix bracket
-// (mode 1) for every vector that needs it: one CTA of kFinishThreads threads,
+// (mode 1) of vector v, if it needs it: one CTA of kFinishThreads threads,
 // the candidates staged in its shared memory when they fit (kFinishStage
 // floats), narrowed on the float keys and finished by Michelot's step (see
 // l1_window_finish).  A single CTA walking a list of a few hundred thousand
 // candidates is bound by the latency of its loads, so it runs apart from the
-// main pass with the most threads a CTA can have.  parts: the main pass's
-// CTAs (mode 0: their count and sum above the window in pn / ps).
+// main pass with the most threads a CTA can have, and the vectors' searches
+// (independent) run in CTAs of their own.  parts: the main pass's CTAs (mode
+// 0: their count and sum above the window in pn / ps).
 constexpr int kFinishThreads = 1024;
 constexpr unsigned kFinishStage = 32768;
 constexpr size_t kFinishSmem = kFinishStage * sizeof(float) + 3 * kNarrowBins * sizeof(unsigned);
 __device__ __forceinline__ void finish_body(const SearchArgs& a, int mode, const unsigned long long* pn,
-                                            const double* ps, int parts) {
+                                            const double* ps, int parts, const int v) {
     extern __shared__ __align__(16) float fstage[];         // kFinishStage floats + the narrowing scratch
     __shared__ double red_d[64];
     __shared__ unsigned long long red_u[64];
     const int want = mode == 0 ? NEED_WINDOW : NEED_GATHER;
     unsigned* scr = reinterpret_cast<unsigned*>(fstage + kFinishStage);
-    for (int v = 0; v < a.nvec; ++v) {
+    if (v >= a.nvec) return;
+    {
         L1Ctl& C = a.sc->ctl[v];
-        if (C.need != want) continue;                       // uniform over the CTA
+        if (C.need != want) return;                         // uniform over the CTA
         const double r = a.sc->radius[v];
         const unsigned m = __ldcg(&a.sc->acc[v].m);
         const double lo = C.g_lo, hi = C.g_hi;
@@ -533,7 +551,8 @@ __device__ __forceinline__ void finish_body(const SearchArgs& a, int mode, const
         }
         double tau = 0.0;
         const int rc = l1_window_finish(n, sm, a.w.cand[v], m, lo, hi, r, &tau, red_d, red_u, nullptr, fstage,
-                                        kFinishStage, scr);
+                                        kFinishStage, scr, narrow_pre(a.w, v, m));
+        narrow_clear(a.w, v);
         if (threadIdx.x == 0) {
             if (mode == 0) {
                 if (rc == 0) {
@@ -549,7 +568,7 @@ __device__ __forceinline__ void finish_body(const SearchArgs& a, int mode, const
                     // the next bin's edge: every value of the bin is inactive
                     tau = (sm - r) / n;
                 } else if (rc != 0) {
-                    a.sc->error |= 2;
+                    atomicOr(&a.sc->error, 2);
                 }
                 l1_record_tau(C, tau, (double)min(m, kCandCap), hi - lo, false);
             }
@@ -559,10 +578,11 @@ __device__ __forceinline__ void finish_body(const SearchArgs& a, int mode, const
     }
 }
 
+// one CTA per vector
 __global__ void __launch_bounds__(kFinishThreads) k_search_finish(const SearchArgs a, int mode,
                                                                    const unsigned long long* pn,
                                                                    const double* ps, int parts) {
-    finish_body(a, mode, pn, ps, parts);
+    finish_body(a, mode, pn, ps, parts, blockIdx.x);
 }
 
 // out = soft(x, tau) for the standalone projection
@@ -811,12 +831,12 @@ __global__ void __launch_bounds__(NT) k_gather_batch(const __grid_constant__ Sea
     if (__ldcg(&q.a.sc->done)) return;
     gather_body(q.src, q.a, blockIdx.x - t.start[c], t.start[c + 1] - t.start[c]);
 }
-// one CTA per cube
+// one CTA per cube and vector
 __global__ void __launch_bounds__(kFinishThreads) k_finish_batch(const __grid_constant__ SearchBatchTab t,
                                                                   const int mode) {
-    const SearchCube& q = t.c[blockIdx.x];
+    const SearchCube& q = t.c[blockIdx.x >> 1];
     if (__ldcg(&q.a.sc->done)) return;
-    finish_body(q.a, mode, q.pn, q.ps, q.parts);
+    finish_body(q.a, mode, q.pn, q.ps, q.parts, blockIdx.x & 1);
 }
 __global__ void __launch_bounds__(NT) k2_batch(const __grid_constant__ K2BatchTab t) {
     const int c = batch_cube_of(t.start, t.n, blockIdx.x);
@@ -888,7 +908,7 @@ int light_configure(int storage) {
 int launch_search_finish(int mode, Scal* sc, const L1Work& w, int nvec, const unsigned long long* pn,
                          const double* ps, int parts, cudaStream_t st) {
     SearchArgs a{sc, w, nvec};
-    k_search_finish<<<1, kFinishThreads, kFinishSmem, st>>>(a, mode, pn, ps, parts);
+    k_search_finish<<<nvec, kFinishThreads, kFinishSmem, st>>>(a, mode, pn, ps, parts);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -975,7 +995,7 @@ int launch_gather_batch(const BatchCube* cubes, int n, cudaStream_t st) {
 int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st) {
     SearchBatchTab t{};
     if (search_table(cubes, n, t, [](const BatchCube&, const SlabPart&) { return 1; }) < 0) return -1;
-    k_finish_batch<<<n, kFinishThreads, kFinishSmem, st>>>(t, mode);
+    k_finish_batch<<<2 * n, kFinishThreads, kFinishSmem, st>>>(t, mode);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -479,12 +479,14 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
             append_shared(ct_, x_t, cbuf + L::CB, ccnt + 1, a.l1.cand[1], &a.sc->acc[1].m);
         }
         if constexpr (HIST) {
-            // one voxel per warp and band (the lane rotates with the band and
-            // the warp) goes into the histogram: a 1/32 sample spread over the
-            // tile's rows, and no two lanes of a warp contend for one counter
-            const bool samp = valid_t && (threadIdx.x & 31) == ((unsigned)(b * 13 + (tid >> 5) * 7) & 31u);
-            hist_add(W.hs && samp, x_s, W.hb_s, hsm, S.top_s);
-            hist_add(W.ht && samp, x_t, W.hb_t, hsm + kK1Bins / 2, S.top_t);
+            // a 1/32 sample: a warp (one row of the tile) counts its 32 voxels
+            // at one band in 32, the band rotating with the row and the tile
+            // so that every band is sampled; the branch is warp-uniform, so
+            // the other 31 band steps cost one test
+            if ((((unsigned)b + 7u * (unsigned)r_t + 5u * (unsigned)(i0 >> 4) + 3u * (unsigned)(j0 >> 5)) & 31u) == 0u) {
+                hist_add(W.hs && valid_t, x_s, W.hb_s, hsm, S.top_s);
+                hist_add(W.ht && valid_t, x_t, W.hb_t, hsm + kK1Bins / 2, S.top_t);
+            }
         }
     };
 
@@ -569,6 +571,8 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
     __shared__ unsigned long long red_u[64];
     __shared__ unsigned ccnt[2], cbase[2];
     __shared__ int is_last, sh_flag;
+    __shared__ unsigned long long tail_n[4];
+    __shared__ double tail_s[4];
     const Geom& g = a.g;
     const IterParams& P = a.p;
     const int i0 = by * L::TY, j0 = bx * L::TX;
@@ -639,6 +643,20 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
             const unsigned n = min(ccnt[v], (unsigned)L::CB);
             for (unsigned k = tid; k < n; k += L::NT)
                 if (cbase[v] + k < kCandCap) a.l1.cand[v][cbase[v] + k] = cbuf[v * L::CB + k];
+            // and into the list's key histogram over the window, which the
+            // finish then narrows without another pass over the candidates
+            // (values that overflowed the buffer are not counted: the finish
+            // then bins the list itself)
+            const bool on = v == 0 ? W.s : W.t;
+            if (on && a.l1.nh) {
+                const NarrowGeom ng = narrow_geom(__float_as_uint(v == 0 ? W.lo_s : W.lo_t),
+                                                  __float_as_uint(v == 0 ? W.hi_s : W.hi_t));
+                if (ng.ok) {
+                    unsigned* h = a.l1.nh + v * 3 * kNarrowBins;
+                    for (unsigned k = tid; k < n; k += L::NT) narrow_add(h, ng, __float_as_uint(cbuf[v * L::CB + k]));
+                    if (tid == 0 && n) atomicAdd(a.l1.nbinned + v, n);
+                }
+            }
         }
         if (W.hs || W.ht) {
             // the histogram joins the global one (unpacked, nonzero bins only)
@@ -698,6 +716,28 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
     __syncthreads();
     if (!is_last) return;
     __threadfence();
+    // every CTA's partial counts and sums, both vectors and both statistics
+    // at once (four 16-byte loads per CTA, independent)
+    unsigned long long pn4[4] = {0, 0, 0, 0};
+    double ps4[4] = {0.0, 0.0, 0.0, 0.0};
+    if (W.s || W.t) {
+        const ulonglong2* n2 = reinterpret_cast<const ulonglong2*>(a.l1.k1_n);
+        const double2* s2 = reinterpret_cast<const double2*>(a.l1.k1_s);
+#pragma unroll 4
+        for (int k = tid; k < ncta; k += L::NT) {
+            const ulonglong2 na = __ldcg(n2 + 2 * k), nb = __ldcg(n2 + 2 * k + 1);
+            const double2 sa = __ldcg(s2 + 2 * k), sb = __ldcg(s2 + 2 * k + 1);
+            pn4[0] += na.x; pn4[1] += na.y; pn4[2] += nb.x; pn4[3] += nb.y;
+            ps4[0] += sa.x; ps4[1] += sa.y; ps4[2] += sb.x; ps4[3] += sb.y;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pn4[q] = block_sum(pn4[q], red_u);
+            ps4[q] = block_sum(ps4[q], red_d);
+            if (tid == 0) { tail_n[q] = pn4[q]; tail_s[q] = ps4[q]; }
+        }
+        __syncthreads();
+    }
     for (int v = 0; v < 2; ++v) {
         L1Ctl& C = a.sc->ctl[v];
         const double r = a.sc->radius[v];
@@ -717,14 +757,8 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
             }
             continue;
         }
-        unsigned long long n = 0;
-        double s = 0.0;
-        for (int k = tid; k < ncta; k += L::NT) {
-            n += __ldcg(a.l1.k1_n + 4 * k + v);
-            s += __ldcg(a.l1.k1_s + 4 * k + v);
-        }
-        n = block_sum(n, red_u);
-        s = block_sum(s, red_d);
+        const unsigned long long n = tail_n[v];
+        const double s = tail_s[v];
         const unsigned m = __ldcg(&a.sc->acc[v].m);
         const double tlo = C.theta_lo, thi = C.theta_hi;
         double tau = 0.0;
@@ -734,7 +768,9 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
         constexpr int kScr = 3 * kNarrowBins * 4;
         const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi,
                                           reinterpret_cast<float*>(sm), (L::OFF_HIST - kScr) / 4,
-                                          reinterpret_cast<unsigned*>(sm + L::OFF_HIST - kScr));
+                                          reinterpret_cast<unsigned*>(sm + L::OFF_HIST - kScr),
+                                          narrow_pre(a.l1, v, m));
+        narrow_clear(a.l1, v);
         // after a miss, the histogram (when on) brackets the root for one
         // retry pass over the bracket
         const bool hist_v = v == 0 ? W.hs : W.ht;
@@ -742,14 +778,8 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
         float h_lo = 0.f, h_hi = 0.f;
         double h_m = 0.0;
         if (miss && hist_v) {
-            unsigned long long hn = 0;
-            double hs = 0.0;
-            for (int k = tid; k < ncta; k += L::NT) {
-                hn += __ldcg(a.l1.k1_n + 4 * k + 2 + v);
-                hs += __ldcg(a.l1.k1_s + 4 * k + 2 + v);
-            }
-            hn = block_sum(hn, red_u);
-            hs = block_sum(hs, red_d);
+            const unsigned long long hn = tail_n[2 + v];
+            const double hs = tail_s[2 + v];
             hist_hit = l1_hist_bracket(a.l1.khist + v * kK1Bins, v == 0 ? W.hb_s : W.hb_t, (double)hn, hs, r,
                                        (double)kHistSample, &h_lo, &h_hi, &h_m, &sh_flag,
                                        reinterpret_cast<unsigned*>(sm + L::OFF_HIST));
