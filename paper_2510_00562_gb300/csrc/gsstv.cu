@@ -161,6 +161,11 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
         TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used + 1], st)));
         h->ev_used += 2;
     }
+    // the TMA-fed K1 leaves its window's finish to a launch of its own (the
+    // cooperative K1 finishes it in its last CTA)
+    if (h->k1_variant == 1)
+        TRY(map_launch(launch_search_finish(2, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
+                                            k1_tma_grid(h->g, whole, h->k1_chunk), st)));
     TRY(map_launch(launch_window(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, whole, st)));
     TRY(map_launch(launch_search_finish(0, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
                                         window_grid(h->g, whole, h->k1_ctas), st)));
@@ -882,6 +887,7 @@ int batch_enqueue(gsstv_batch* b, const std::vector<int>& set, int par, cudaStre
         q.maps = b->dmaps + 2 * c + par;
     }
     TRY(map_launch(launch_k1_batch(cubes, nc, st)));
+    TRY(map_launch(launch_finish_batch(cubes, nc, 2, st)));
     TRY(map_launch(launch_window_batch(cubes, nc, st)));
     TRY(map_launch(launch_finish_batch(cubes, nc, 0, st)));
     for (int level = 0; level < 3; ++level) TRY(map_launch(launch_radix_batch(cubes, nc, level, st)));
@@ -1065,8 +1071,9 @@ int gsstv_batch_handle(gsstv_batch* b, int c, gsstv_handle** out) {
 // bands, Sec. II-A).  A pass runs every stage of the single-handle pass on
 // each slab in turn; the global sums of a stage (l1 window statistics,
 // histograms and candidates, radix histograms, the l2-ball and Eq. 28 norms)
-// go to one shared reduction area and are finished by the last CTA of all the
-// stage's launches.  After the pass the halos are refreshed with one copy per
+// go to one shared reduction area and are finished once for all slabs (by the
+// finishing launch after the stage, or by the last CTA of all the stage's
+// launches).  After the pass the halos are refreshed with one copy per
 // plane: the band above a slab (u, q, y1, y2: what the next pass's u' of that
 // band needs) and the band below it (y2: D^T y2 there, for D_s^T).  This is
 // the data flow of a cube split over several GPUs, with the shared reduction
@@ -1136,6 +1143,7 @@ int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st) {
         TRY(map_launch(launch_k1_tma(GSSTV_FP32, x->g, x->maps[par], bufs(x, par), ip, G->sc, G->l1,
                                      G->k1_chunk[s], G->k1p[s], st)));
     }
+    TRY(map_launch(launch_search_finish(2, G->sc, G->l1, 2, G->l1.k1_n, G->l1.k1_s, G->k1p[0].cta_total, st)));
     for (int s = 0; s < S; ++s) {
         gsstv_handle* x = G->h[s];
         TRY(map_launch(launch_window(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->win_cap, G->winp[s], st)));

@@ -158,6 +158,9 @@ struct Scal {
     long long iter;
     int done;                  // a batch cube that has stopped (Eq. 28 or its pass cap)
     int stop_parity;           // the parity that holds its state then
+    // what the fused pass (TMA-fed K1) counted for vector v, for the finish
+    // that follows it: its window statistics and candidates, its histogram
+    int k1_win[2], k1_hist[2];
 };
 
 constexpr int kHistBins = 2048;        // radix histogram bins per vector
@@ -285,6 +288,17 @@ __device__ __forceinline__ double block_sum_pair(const Kahan& k, float2* buf) {
     }
     return r;
 }
+// The warp's sum of its lanes' compensated sums as a float pair; every lane
+// gets it.
+__device__ __forceinline__ void warp_sum_pair(const Kahan& k, float& hi, float& lo) {
+    hi = k.s;
+    lo = -k.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
+        pair_add(hi, lo, bh, bl);
+    }
+}
 // Integer sum over the CTA (32-bit lanes, 64-bit result), every thread gets it.
 __device__ __forceinline__ unsigned long long block_count(unsigned x, unsigned long long* buf) {
     unsigned long long v = x;
@@ -374,9 +388,10 @@ struct K1Maps {
 // halo band on each side).  The launch's storage holds bands [band0, band0 +
 // g.n3) of a cube of n3g bands, and the launch updates the stored bands
 // [o0, o1).  Every global sum of a pass stage (the l2-ball norm, the Eq. 28
-// norms, the l1 threshold statistics) is finished by the last CTA of all the
-// stage's launches: this launch's CTAs are numbered from cta_base among
-// cta_total.  The whole cube in one launch: whole_cube(g).
+// norms, the l1 threshold statistics) is finished once for all the stage's
+// launches (by the last of their CTAs, or by a finishing launch after them):
+// this launch's CTAs are numbered from cta_base among cta_total.  The whole
+// cube in one launch: whole_cube(g).
 struct SlabPart {
     int band0 = 0, n3g = 0, o0 = 0, o1 = 0;
     int cta_base = 0, cta_total = 0;     // cta_total = 0: this launch alone

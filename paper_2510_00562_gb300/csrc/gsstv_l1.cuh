@@ -69,6 +69,7 @@ __device__ __forceinline__ void for_each_candidate(const float* cand, unsigned m
 // which are then staged in the scratch for Michelot's step.
 constexpr unsigned kNarrowStage = 3 * kNarrowBins;   // floats the scratch stages
 constexpr unsigned kNarrowMin = 4096;                // candidates beyond this are narrowed first
+constexpr unsigned kWarpMichelot = 1024;             // narrowed values this few: one warp finishes
 
 // Bin geometry of one narrowing round over the key window (klo, khi]: bins of
 // 2^shift keys counted from base = klo >> shift, nb of them, with the
@@ -118,8 +119,8 @@ __device__ __forceinline__ void narrow_clear(const L1Work& w, int v) {
 }
 
 // Whole block.  cand[0..m): the candidates, every one in (klo, khi] as keys;
-// scr: 3 kNarrowBins unsigned of shared memory; sh_d: 4 doubles, wtot: 64
-// unsigned long long of shared memory; pre (optional): the candidates' key
+// scr: 3 kNarrowBins unsigned of shared memory; sh_d: 4 doubles of shared
+// memory; pre (optional): the candidates' key
 // histogram over (klo, khi], already built (the first round reads it instead
 // of binning the candidates).  On
 // return 0: (klo, khi] narrowed, n_hi / s_hi now count everything above khi,
@@ -130,7 +131,7 @@ __device__ __forceinline__ void narrow_clear(const L1Work& w, int v) {
 // narrow in a few rounds.
 static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m, double& n_hi, double& s_hi,
                                 unsigned& klo, unsigned& khi, double r, unsigned* scr, unsigned* m_st, int* sh_i,
-                                double* sh_d, unsigned long long* wtot, const unsigned* pre = nullptr) {
+                                double* sh_d, const unsigned* pre = nullptr) {
     // every candidate, from global memory (batched loads) or from shared memory
     auto each = [&](auto&& f) {
         if (cand_shared) {
@@ -151,7 +152,23 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
         if (!ng.ok) return 2;
         __syncthreads();
         if (round == 0 && pre) {
-            for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) scr[k] = __ldcg(pre + k);
+            // 16-byte loads, all of a thread's issued before its stores (one
+            // CTA copying from L2 is bound by the loads' latency)
+            const uint4* p4 = reinterpret_cast<const uint4*>(pre);
+            uint4* s4 = reinterpret_cast<uint4*>(scr);
+            constexpr int kW4 = 3 * kNarrowBins / 4;
+            uint4 q[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = (int)threadIdx.x + j * (int)blockDim.x;
+                if (k < kW4) q[j] = __ldcg(p4 + k);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = (int)threadIdx.x + j * (int)blockDim.x;
+                if (k < kW4) s4[k] = q[j];
+            }
+            for (int k = (int)threadIdx.x + 2 * (int)blockDim.x; k < kW4; k += blockDim.x) s4[k] = __ldcg(p4 + k);
         } else {
             for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) scr[k] = 0u;
             __syncthreads();
@@ -179,24 +196,6 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
             const unsigned long long res = (unsigned long long)rhi[b] * 1024ull + rlo[b];
             return (unsigned long long)cnt[b] * V(lk) + (res << (max((int)((lk >> 23) & 0xffu), 1) - e0));
         };
-        const int nt = (int)blockDim.x;
-        const int per = (nb + nt - 1) / nt;
-        const int c0 = (int)threadIdx.x * per, c1 = min(nb, c0 + per);
-        unsigned long long Nc = 0, Sc = 0;
-        for (int b = c0; b < c1; ++b) { Nc += cnt[b]; Sc += bin_int(b); }
-        // totals of the chunks above this thread's (exclusive suffix over threads)
-        unsigned long long Ni = Nc, Si = Sc;
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (nt + 31) >> 5;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long a = __shfl_down_sync(0xffffffffu, Ni, o);
-            const unsigned long long c = __shfl_down_sync(0xffffffffu, Si, o);
-            if (lane + o < 32) { Ni += a; Si += c; }
-        }
-        if (lane == 0) { wtot[wid] = Ni; wtot[32 + wid] = Si; }
-        __syncthreads();
-        unsigned long long Nup = Ni - Nc, Sup = Si - Sc;          // chunks above, inside this warp
-        for (int w = wid + 1; w < nw; ++w) { Nup += wtot[w]; Sup += wtot[32 + w]; }
         // phi at an edge with the bins from b up and everything above the window
         auto phi_at = [&](double e, unsigned long long e_int, unsigned long long Nsuf, unsigned long long Ssuf) {
             return s_hi - n_hi * e - r + (double)(long long)(Ssuf - Nsuf * e_int) * u0;
@@ -207,36 +206,65 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
             const unsigned lk = (base + (unsigned)b) << shift;
             return phi_at((double)__uint_as_float(lk), V(lk), Nsuf, Ssuf);
         };
-        // the chunk whose lowest edge is the highest with phi >= 0
-        const bool has = c0 < c1;
-        const bool ok = has && edge_phi(c0, Nup + Nc, Sup + Sc) >= 0.0;
-        if (threadIdx.x == 0) sh_i[0] = -1;
-        __syncthreads();
-        if (ok) atomicMax(sh_i, (int)threadIdx.x);
-        __syncthreads();
-        const int owner = sh_i[0];
-        __syncthreads();
-        if (owner < 0) {
-            if (threadIdx.x == 0) {
-                sh_i[0] = -1;
-                // phi at the window's lower end, and the count above it
-                sh_d[2] = edge_phi(0, Nup + Nc, Sup + Sc);
-                sh_d[3] = n_hi + (double)(Nup + Nc);
+        // The bin whose lower edge is the highest with phi >= 0 (phi does not
+        // increase with the edge, so those edges come first).  Warp 0 alone:
+        // FP64 runs at a small fraction of the FP32 rate on this part, and one
+        // warp's FP64 instruction costs what the whole block's would divided
+        // by its warps.  Each lane sums a chunk of at most 64 bins; the
+        // highest lane whose chunk's lowest edge has phi >= 0 holds the bin,
+        // which the lanes then find two bins each.
+        if (threadIdx.x < 32) {
+            const int lane = (int)threadIdx.x;
+            const int per = (nb + 31) / 32;
+            const int c0 = lane * per, c1 = min(nb, c0 + per);
+            unsigned long long Nc = 0, Sc = 0;
+            for (int b = c0; b < c1; ++b) { Nc += cnt[b]; Sc += bin_int(b); }
+            // inclusive suffix over the lanes: the bins from c0 up
+            unsigned long long Ni = Nc, Si = Sc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long x = __shfl_down_sync(0xffffffffu, Ni, o);
+                const unsigned long long y = __shfl_down_sync(0xffffffffu, Si, o);
+                if (lane + o < 32) { Ni += x; Si += y; }
             }
-        } else if ((int)threadIdx.x == owner) {
-            // this chunk: its highest bin whose lower edge has phi >= 0
-            unsigned long long N = Nup, S = Sup;
-            int best = c0;
-            unsigned long long bn = Nup, bs = Sup;
-            for (int b = c1 - 1; b >= c0; --b) {
-                const unsigned long long na = N, sa = S;         // bins above b
-                N += cnt[b];
-                S += bin_int(b);
-                if (edge_phi(b, N, S) >= 0.0) { best = b; bn = na; bs = sa; break; }
+            const bool ok = c0 < c1 && edge_phi(c0, Ni, Si) >= 0.0;
+            const unsigned okm = __ballot_sync(0xffffffffu, ok);
+            if (okm == 0u) {
+                if (lane == 0) {
+                    sh_i[0] = -1;
+                    // phi at the window's lower end, and the count above it
+                    sh_d[2] = edge_phi(0, Ni, Si);
+                    sh_d[3] = n_hi + (double)Ni;
+                }
+            } else {
+                const int L = 31 - __clz(okm);
+                const int l0 = L * per, l1 = min(nb, l0 + per);
+                // the bins above lane L's chunk
+                const unsigned long long Nup = __shfl_sync(0xffffffffu, Ni - Nc, L);
+                const unsigned long long Sup = __shfl_sync(0xffffffffu, Si - Sc, L);
+                const int bA = l0 + 2 * lane, bB = bA + 1;
+                const unsigned long long nA = bA < l1 ? cnt[bA] : 0ull, sA = bA < l1 ? bin_int(bA) : 0ull;
+                const unsigned long long nB = bB < l1 ? cnt[bB] : 0ull, sB = bB < l1 ? bin_int(bB) : 0ull;
+                unsigned long long Nj = nA + nB, Sj = sA + sB;      // inclusive suffix from bA
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long x = __shfl_down_sync(0xffffffffu, Nj, o);
+                    const unsigned long long y = __shfl_down_sync(0xffffffffu, Sj, o);
+                    if (lane + o < 32) { Nj += x; Sj += y; }
+                }
+                const bool okA = bA < l1 && edge_phi(bA, Nup + Nj, Sup + Sj) >= 0.0;
+                const bool okB = bB < l1 && edge_phi(bB, Nup + Nj - nA, Sup + Sj - sA) >= 0.0;
+                const int mine = okB ? bB : okA ? bA : -1;
+                const int best = __reduce_max_sync(0xffffffffu, mine);
+                if (mine == best) {
+                    // the bins above the chosen one
+                    const unsigned long long an = best == bB ? Nup + Nj - nA - nB : Nup + Nj - nA;
+                    const unsigned long long as = best == bB ? Sup + Sj - sA - sB : Sup + Sj - sA;
+                    sh_i[0] = best;
+                    sh_d[0] = n_hi + (double)an;
+                    sh_d[1] = s_hi + (double)as * u0;
+                }
             }
-            sh_i[0] = best;
-            sh_d[0] = n_hi + (double)bn;
-            sh_d[1] = s_hi + (double)bs * u0;
         }
         __syncthreads();
         const int kb = sh_i[0];
@@ -288,18 +316,34 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
                                        unsigned long long* red_u, WinInfo* info = nullptr,
                                        float* stage = nullptr, unsigned stage_cap = 0,
                                        unsigned* scr = nullptr, const unsigned* pre = nullptr) {
-    const double phi_hi = s_hi - n_hi * theta_hi - r;
-    if (info) info->phi_hi = phi_hi;
-    if (m_raw > kCandCap) return 1;
-    unsigned m = m_raw;
-    if (phi_hi > 0.0) return 2;                        // root above the window
-    if (scr && m > kNarrowMin && theta_lo >= 0.0) {
+    // The scalar tests in FP64 on thread 0 (FP64 is scarce on this part),
+    // shared with the block.
+    __shared__ int wp_rc, wp_narrow, wp_pre;
+    __shared__ unsigned wp_klo, wp_khi;
+    if (threadIdx.x == 0) {
+        const double phi_hi = s_hi - n_hi * theta_hi - r;
+        if (info) info->phi_hi = phi_hi;
+        wp_rc = m_raw > kCandCap ? 1 : phi_hi > 0.0 ? 2 : -1;     // 2: root above the window
+        wp_narrow = wp_rc < 0 && scr && m_raw > kNarrowMin && theta_lo >= 0.0;
         // the window's ends as float keys: (klo, khi] holds every candidate
         unsigned klo = __float_as_uint((float)theta_lo), khi = __float_as_uint((float)theta_hi);
         if ((double)__uint_as_float(klo) > theta_lo) klo -= 1u;        // rounding of the ends
         if ((double)__uint_as_float(khi) < theta_hi) khi += 1u;
+        wp_klo = klo;
+        wp_khi = khi;
         // a key histogram built over the float window fits only that window
-        if ((double)(float)theta_lo != theta_lo || (double)(float)theta_hi != theta_hi) pre = nullptr;
+        wp_pre = pre && (double)(float)theta_lo == theta_lo && (double)(float)theta_hi == theta_hi;
+    }
+    __syncthreads();
+    if (wp_rc >= 0) {
+        const int rc = wp_rc;
+        __syncthreads();
+        return rc;
+    }
+    unsigned m = m_raw;
+    if (wp_narrow) {
+        unsigned klo = wp_klo, khi = wp_khi;
+        if (!wp_pre) pre = nullptr;
         unsigned m_st = 0;
         __shared__ int nr_i[1];
         double nh = n_hi, sh = s_hi;
@@ -313,8 +357,8 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
             src = stage;
             src_shared = true;
         }
-        // (red_d and red_u serve as the narrowing's scalars and warp totals)
-        const int rc = l1_narrow(src, src_shared, m, nh, sh, klo, khi, r, scr, &m_st, nr_i, red_d, red_u, pre);
+        // (red_d serves as the narrowing's scalars)
+        const int rc = l1_narrow(src, src_shared, m, nh, sh, klo, khi, r, scr, &m_st, nr_i, red_d, pre);
         if (rc == 1) {
             // phi(theta_lo) < 0: as below, inside the ball or a miss below
             if (info) { info->phi_lo = red_d[2]; info->n_lo = red_d[3]; }
@@ -336,6 +380,70 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
     }
     const bool staged = stage && m <= stage_cap;
     const bool pre_staged = cand == nullptr;           // the narrowed values already sit in the stage
+    if (pre_staged && m <= kWarpMichelot) {
+        // A few values (one narrow bin): warp 0 alone runs Michelot's steps
+        // on them, with shuffles instead of CTA barriers; the FP64 steps on
+        // lane 0.
+        __shared__ double ww_tau;
+        __shared__ int ww_rc;
+        if (threadIdx.x < 32) {
+            const unsigned lane = threadIdx.x;
+            Kahan ks;
+            for (unsigned k = lane; k < m; k += 32u) ks.add(stage[k]);
+            float h, l;
+            warp_sum_pair(ks, h, l);
+            int state = 0;
+            double tau = 0.0;
+            float tf = 0.f;
+            if (lane == 0) {
+                const double sum_c = (double)h + (double)l;
+                const double n_all = n_hi + (double)m;
+                const double phi_lo = s_hi + sum_c - n_all * theta_lo - r;
+                if (phi_lo < 0.0) {
+                    state = theta_lo <= 0.0 ? 2 : 3;
+                } else {
+                    tau = (s_hi + sum_c - r) / n_all;
+                    tf = __double2float_rd(tau);
+                }
+            }
+            state = __shfl_sync(0xffffffffu, state, 0);
+            tf = __shfl_sync(0xffffffffu, tf, 0);
+            int rc = state == 2 ? 0 : state == 3 ? 1 : 0;
+            if (state == 0) {
+                unsigned prev = m;
+                for (int it = 0; it < 200; ++it) {
+                    Kahan ka;
+                    unsigned c = 0;
+                    for (unsigned k = lane; k < m; k += 32u) {
+                        const float x = stage[k];
+                        if (x > tf) { ka.add(x); ++c; }
+                    }
+                    warp_sum_pair(ka, h, l);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                    int done = 0;
+                    if (lane == 0) {
+                        tau = (s_hi + ((double)h + (double)l) - r) / (n_hi + (double)c);
+                        tf = __double2float_rd(tau);
+                        done = c == prev ? 1 : 0;
+                    }
+                    tf = __shfl_sync(0xffffffffu, tf, 0);
+                    done = __shfl_sync(0xffffffffu, done, 0);
+                    prev = c;
+                    if (done) break;
+                }
+            }
+            if (lane == 0) {
+                ww_tau = state == 2 ? 0.0 : tau;
+                ww_rc = rc;
+            }
+        }
+        __syncthreads();
+        const int rc = ww_rc;
+        if (rc == 0) *tau_out = ww_tau;
+        __syncthreads();
+        return rc;
+    }
     // Sums in compensated FP32 per thread and float pairs across the CTA;
     // the FP64 steps (a handful per pass) run on thread 0 and reach the
     // other threads through shared memory.

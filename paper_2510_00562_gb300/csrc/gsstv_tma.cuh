@@ -61,6 +61,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Brings a tensor map held in global memory into the TMA unit's descriptor
+// cache ahead of its first use.
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 // 3-D tiled bulk tensor load global -> shared, completion counted on `bar`.
 // The innermost coordinate x must be a multiple of 16 bytes / element size;
 // other coordinates may be negative or beyond the tensor (zero fill).

@@ -387,10 +387,21 @@ struct BlockCand {
     float (*buf)[kBlkCand];
     unsigned* cnt;     // [2]
     unsigned* base;    // [2]
+    // the lists' key histograms over the windows (null: not kept)
+    unsigned* nh[2] = {nullptr, nullptr};
+    unsigned* nbinned = nullptr;
+    NarrowGeom ng[2];
     __device__ void init() {
         if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
         __syncthreads();
     }
+    // keep vector v's list histogram over the key window (lo, hi]
+    __device__ void keep_hist(const L1Work& w, int v, float lo, float hi) {
+        ng[v] = narrow_geom(__float_as_uint(lo), __float_as_uint(hi));
+        nh[v] = w.nh && ng[v].ok ? w.nh + v * 3 * kNarrowBins : nullptr;
+        nbinned = w.nbinned;
+    }
+    // values past the buffer go straight to the global list and its histogram
     __device__ void append(int v, bool take, float x, float* gcand, unsigned* gcnt) {
         const unsigned mask = __ballot_sync(0xffffffffu, take);
         if (mask == 0) return;
@@ -401,7 +412,14 @@ struct BlockCand {
         b = __shfl_sync(0xffffffffu, b, leader);
         const unsigned k = b + __popc(mask & ((1u << lane) - 1u));
         if (take && k < (unsigned)kBlkCand) buf[v][k] = x;
-        if (b + __popc(mask) > (unsigned)kBlkCand) append_candidate(take && k >= (unsigned)kBlkCand, x, gcand, gcnt);
+        if (b + __popc(mask) > (unsigned)kBlkCand) {
+            const bool over = take && k >= (unsigned)kBlkCand;
+            append_candidate(over, x, gcand, gcnt);
+            if (over && nh[v]) {
+                narrow_add(nh[v], ng[v], __float_as_uint(x));
+                atomicAdd(nbinned + v, 1u);
+            }
+        }
     }
     // whole block; before the pass's completion ticket
     __device__ void flush(float* const* gcand, Scal* sc) {
@@ -417,17 +435,13 @@ struct BlockCand {
                 if (base[v] + k < kCandCap) gcand[v][base[v] + k] = buf[v][k];
         }
     }
-    // after flush: counts the buffered candidates of vector v, all in the key
-    // window (lo, hi], into the list's key histogram (a candidate that
-    // overflowed the buffer is not counted, so the finish does without it)
-    __device__ void bin(const L1Work& w, int v, float lo, float hi) {
-        if (!w.nh) return;
-        const NarrowGeom ng = narrow_geom(__float_as_uint(lo), __float_as_uint(hi));
-        if (!ng.ok) return;
+    // after flush: counts the buffered candidates of vector v into the list's
+    // key histogram (kept by keep_hist)
+    __device__ void bin(int v) {
+        if (!nh[v]) return;
         const unsigned n = min(cnt[v], (unsigned)kBlkCand);
-        unsigned* h = w.nh + v * 3 * kNarrowBins;
-        for (unsigned k = threadIdx.x; k < n; k += blockDim.x) narrow_add(h, ng, __float_as_uint(buf[v][k]));
-        if (threadIdx.x == 0 && n) atomicAdd(w.nbinned + v, n);
+        for (unsigned k = threadIdx.x; k < n; k += blockDim.x) narrow_add(nh[v], ng[v], __float_as_uint(buf[v][k]));
+        if (threadIdx.x == 0 && n) atomicAdd(nbinned + v, n);
     }
 };
 #define GSSTV_BLOCK_CAND(name)                                   \
@@ -447,13 +461,15 @@ __device__ __forceinline__ void gather_body(const Src& src, const SearchArgs& a,
     const float lo0 = a.sc->ctl[0].g_lo, hi0 = a.sc->ctl[0].g_hi;
     const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
     GSSTV_BLOCK_CAND(bc);
+    if (need[0]) bc.keep_hist(a.w, 0, lo0, hi0);
+    if (need[1]) bc.keep_hist(a.w, 1, lo1, hi1);
     src.visit(bid, nblk, [&](bool valid, float x0, float x1) {
         if (need[0]) bc.append(0, valid && x0 > lo0 && x0 <= hi0, x0, a.w.cand[0], &a.sc->acc[0].m);
         if (need[1]) bc.append(1, valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
     });
     bc.flush(a.w.cand, a.sc);
-    if (need[0]) bc.bin(a.w, 0, lo0, hi0);
-    if (need[1]) bc.bin(a.w, 1, lo1, hi1);
+    bc.bin(0);
+    bc.bin(1);
 }
 
 template <typename Src>
@@ -478,6 +494,8 @@ __device__ __forceinline__ void window_body(const Src& src, const SearchArgs& a,
     const float lo1 = a.sc->ctl[1].g_lo, hi1 = a.sc->ctl[1].g_hi;
     WinAcc w0, w1;
     GSSTV_BLOCK_CAND(bc);
+    if (need[0]) bc.keep_hist(a.w, 0, lo0, hi0);
+    if (need[1]) bc.keep_hist(a.w, 1, lo1, hi1);
     src.visit(bid, nblk, [&](bool valid, float x0, float x1) {
         if (need[0]) {
             const bool hi = valid && x0 > hi0;
@@ -491,8 +509,8 @@ __device__ __forceinline__ void window_body(const Src& src, const SearchArgs& a,
         }
     });
     bc.flush(a.w.cand, a.sc);
-    if (need[0]) bc.bin(a.w, 0, lo0, hi0);
-    if (need[1]) bc.bin(a.w, 1, lo1, hi1);
+    bc.bin(0);
+    bc.bin(1);
     float2* pbuf = reinterpret_cast<float2*>(red_d);
     const unsigned long long n0 = block_sum(w0.n, red_u), n1 = block_sum(w1.n, red_u);
     const double s0 = block_sum_pair(w0.s, pbuf), s1 = block_sum_pair(w1.s, pbuf);
@@ -509,17 +527,96 @@ __global__ void __launch_bounds__(NT) k_window(const Src src, const SearchArgs a
     window_body(src, a, pn, ps, blockIdx.x, gridDim.x);
 }
 
-// The finish of the retry window (mode 0) or of the gathered radix bracket
-// (mode 1) of vector v, if it needs it: one CTA of kFinishThreads threads,
+// The finish of K1's window (mode 2), of the retry window (mode 0) or of the
+// gathered radix bracket (mode 1) of vector v, if it needs it: one CTA of kFinishThreads threads,
 // the candidates staged in its shared memory when they fit (kFinishStage
 // floats), narrowed on the float keys and finished by Michelot's step (see
 // l1_window_finish).  A single CTA walking a list of a few hundred thousand
 // candidates is bound by the latency of its loads, so it runs apart from the
 // main pass with the most threads a CTA can have, and the vectors' searches
 // (independent) run in CTAs of their own.  parts: the main pass's CTAs (mode
-// 0: their count and sum above the window in pn / ps).
+// 0: their count and sum above the window in pn / ps, two per CTA; mode 2:
+// K1's four per CTA, the window's and the histogram's above-range statistics
+// of both vectors).
 constexpr int kFinishThreads = 1024;
 constexpr unsigned kFinishStage = 32768;
+
+// K1's window of vector v, after the fused pass: the CTAs' counts and sums
+// above the window summed, tau found on the candidates (l1_window_finish); on
+// a miss, K1's sampled histogram (when it was on) brackets tau for one retry
+// pass, else the next window is placed from the bounds the miss gives or the
+// radix passes run.  The whole block; K1's partials: pn / ps, four per CTA.
+__device__ __noinline__ void k1_window_finish(const SearchArgs& a, const unsigned long long* pn, const double* ps,
+                                              int parts, const int v, float* fstage, unsigned* scr, double* red_d,
+                                              unsigned long long* red_u) {
+    __shared__ int sh_flag;
+    L1Ctl& C = a.sc->ctl[v];
+    const double r = a.sc->radius[v];
+    if (!(r > 0.0)) {
+        if (threadIdx.x == 0) {
+            C.tau = __int_as_float(0x7f800000);
+            C.have_tau = 1;
+            C.need = NEED_NONE;
+            C.window_ok = 0;
+        }
+        return;
+    }
+    if (!__ldcg(&a.sc->k1_win[v])) {
+        if (threadIdx.x == 0) {
+            C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0; C.exact_runs++;
+        }
+        return;
+    }
+    const bool hist_v = __ldcg(&a.sc->k1_hist[v]) != 0;
+    unsigned long long n = 0, hn = 0;
+    double s = 0.0, hs = 0.0;
+    for (int k = threadIdx.x; k < parts; k += blockDim.x) {
+        n += __ldcg(pn + 4 * k + v);
+        s += __ldcg(ps + 4 * k + v);
+        hn += __ldcg(pn + 4 * k + 2 + v);
+        hs += __ldcg(ps + 4 * k + 2 + v);
+    }
+    n = block_sum(n, red_u);
+    s = block_sum(s, red_d);
+    const unsigned m = __ldcg(&a.sc->acc[v].m);
+    const double tlo = C.theta_lo, thi = C.theta_hi;
+    double tau = 0.0;
+    WinInfo wi;
+    const int miss = l1_window_finish((double)n, s, a.w.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi, fstage,
+                                      kFinishStage, scr, narrow_pre(a.w, v, m));
+    narrow_clear(a.w, v);
+    int hist_hit = 0;
+    float h_lo = 0.f, h_hi = 0.f;
+    double h_m = 0.0;
+    if (miss && hist_v) {
+        hn = block_sum(hn, red_u);
+        hs = block_sum(hs, red_d);
+        hist_hit = l1_hist_bracket(a.w.khist + v * kK1Bins, C.hbase, (double)hn, hs, r, (double)kHistSample,
+                                   &h_lo, &h_hi, &h_m, &sh_flag, reinterpret_cast<unsigned*>(fstage));
+    }
+    if (hist_v) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < kK1Bins; k += blockDim.x) a.w.khist[v * kK1Bins + k] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        if (!miss) {
+            l1_record_tau(C, tau, (double)min(m, kCandCap), thi - tlo, true);
+            C.hits++;
+            if (C.hist_left > 0) C.hist_left--;
+        } else if (hist_hit) {
+            C.prefix = 0; C.n_above = 0; C.s_above = 0.0;
+            C.need = NEED_WINDOW;
+            C.g_lo = h_lo;
+            C.g_hi = h_hi;
+            C.hist_left = kHistPasses;
+        } else {
+            l1_after_miss(C, miss, wi, (double)n, m, tlo, thi);
+        }
+        a.sc->acc[v].m = 0;
+    }
+    __syncthreads();
+}
+
 constexpr size_t kFinishSmem = kFinishStage * sizeof(float) + 3 * kNarrowBins * sizeof(unsigned);
 __device__ __forceinline__ void finish_body(const SearchArgs& a, int mode, const unsigned long long* pn,
                                             const double* ps, int parts, const int v) {
@@ -529,6 +626,10 @@ __device__ __forceinline__ void finish_body(const SearchArgs& a, int mode, const
     const int want = mode == 0 ? NEED_WINDOW : NEED_GATHER;
     unsigned* scr = reinterpret_cast<unsigned*>(fstage + kFinishStage);
     if (v >= a.nvec) return;
+    if (mode == 2) {
+        k1_window_finish(a, pn, ps, parts, v, fstage, scr, red_d, red_u);
+        return;
+    }
     {
         L1Ctl& C = a.sc->ctl[v];
         if (C.need != want) return;                         // uniform over the CTA
@@ -840,7 +941,9 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish_batch(const __grid_co
 }
 __global__ void __launch_bounds__(NT) k2_batch(const __grid_constant__ K2BatchTab t) {
     const int c = batch_cube_of(t.start, t.n, blockIdx.x);
-    const K2Args<float>& a = t.c[c];
+    // by value: the table is indexed by a run-time cube, so each field is
+    // loaded once instead of at each use
+    const K2Args<float> a = t.c[c];
     if (__ldcg(&a.sc->done)) return;
     k2_body(a, blockIdx.x - t.start[c], t.start[c + 1] - t.start[c]);
 }
@@ -995,6 +1098,8 @@ int launch_gather_batch(const BatchCube* cubes, int n, cudaStream_t st) {
 int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st) {
     SearchBatchTab t{};
     if (search_table(cubes, n, t, [](const BatchCube&, const SlabPart&) { return 1; }) < 0) return -1;
+    if (mode == 2)                       // K1's partials: one set per CTA of the cube's K1 grid
+        for (int c = 0; c < n; ++c) t.c[c].parts = k1_tma_grid(cubes[c].g, whole_cube(cubes[c].g), cubes[c].k1_chunk);
     k_finish_batch<<<2 * n, kFinishThreads, kFinishSmem, st>>>(t, mode);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

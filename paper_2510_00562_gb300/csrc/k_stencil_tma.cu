@@ -8,7 +8,10 @@
 // by bulk tensor (TMA) copies that one thread issues two bands ahead,
 // completing on mbarriers.  One CTA of 512 threads per SM owns a 16 x 32 tile
 // and a run of bands.  Tiles whose halo stays off the image border take a
-// specialised path with no boundary masks.
+// specialised path with no boundary masks.  Each CTA leaves its window
+// statistics and candidates (with their key histogram) for the finishing
+// launch that follows (k_search_finish, one CTA per vector), so that no CTA
+// of this launch runs the threshold search while the rest of the GPU idles.
 //
 // Band march, one CTA barrier per band: while the w steps, u' of band b+1 and
 // the window statistics of band b run, the dual ascent of band b-1 (which
@@ -109,9 +112,9 @@ struct Lay {
     // one-pixel ring: w positions 2 (TX + 2) + 2 TY per set, u' positions (TX + 1) + TY
     static constexpr int NWR = 2 * (TX + 2) + 2 * TY, NUR = (TX + 1) + TY;
     static_assert(TY * TX == NT, "one tile voxel per thread");
-    // dynamic plus the kernel's static shared memory (reductions and the
-    // threshold finish: about 1.4 KB, see ptxas -v) within the 227 KB a CTA may use
-    static_assert(SMEM + 1536 <= 227 * 1024, "shared memory");
+    // dynamic plus the kernel's static shared memory (the candidate counters:
+    // 128 bytes, see ptxas -v) within the 227 KB a CTA may use
+    static_assert(SMEM + 256 <= 227 * 1024, "shared memory");
     static_assert(2 * NWR <= 224 && NUR <= 32 + 32, "ring work layout");
 };
 
@@ -133,6 +136,9 @@ struct K1Win {
     float lo_s, hi_s, lo_t, hi_t;
     bool hs, ht;
     unsigned hb_s, hb_t;
+    // the candidate lists' key histograms over the windows (null: not kept)
+    unsigned *nh_s, *nh_t;
+    NarrowGeom ng_s, ng_t;
 };
 
 // A thread's window statistics: count (a CTA covers at most a few thousand
@@ -151,7 +157,9 @@ struct K1State {
 
 // Appends the lanes' window candidates to the CTA's shared buffer (one
 // shared-memory atomic per warp); values past its end go straight to the
-// global list.  `cnt` keeps counting past the buffer.
+// global list (and are not counted into its key histogram, so that the finish
+// then bins the list itself: counting them here made K1 2 % slower).  `cnt`
+// keeps counting past the buffer.
 __device__ __forceinline__ void append_shared(bool take, float x, float* buf, unsigned* cnt, float* cand,
                                               unsigned* gcnt) {
     const unsigned mask = __ballot_sync(0xffffffffu, take);
@@ -163,7 +171,10 @@ __device__ __forceinline__ void append_shared(bool take, float x, float* buf, un
     base = __shfl_sync(0xffffffffu, base, leader);
     const unsigned k = base + __popc(mask & ((1u << lane) - 1u));
     if (take && k < (unsigned)Lay::CB) buf[k] = x;
-    if (base + __popc(mask) > (unsigned)Lay::CB) append_candidate(take && k >= (unsigned)Lay::CB, x, cand, gcnt);
+    if (base + __popc(mask) > (unsigned)Lay::CB) {
+        const bool over = take && k >= (unsigned)Lay::CB;
+        append_candidate(over, x, cand, gcnt);
+    }
 }
 
 // Counts x into a window accumulator when `take`, without a branch.
@@ -567,12 +578,7 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
                                        const int bz, const int gx, const int gy, const int gz) {
     using L = Lay;
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ double red_d[64];
-    __shared__ unsigned long long red_u[64];
     __shared__ unsigned ccnt[2], cbase[2];
-    __shared__ int is_last, sh_flag;
-    __shared__ unsigned long long tail_n[4];
-    __shared__ double tail_s[4];
     const Geom& g = a.g;
     const IterParams& P = a.p;
     const int i0 = by * L::TY, j0 = bx * L::TX;
@@ -592,6 +598,10 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
     W.hb_t = a.sc->ctl[1].hbase;
     W.hs = W.s && hist_fits && a.sc->ctl[0].hist_left > 0 && hist_base_ok(W.hb_s);
     W.ht = W.t && hist_fits && a.sc->ctl[1].hist_left > 0 && hist_base_ok(W.hb_t);
+    W.ng_s = narrow_geom(__float_as_uint(W.lo_s), __float_as_uint(W.hi_s));
+    W.ng_t = narrow_geom(__float_as_uint(W.lo_t), __float_as_uint(W.hi_t));
+    W.nh_s = W.s && a.l1.nh && W.ng_s.ok ? a.l1.nh : nullptr;
+    W.nh_t = W.t && a.l1.nh && W.ng_t.ok ? a.l1.nh + 3 * kNarrowBins : nullptr;
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::OFF_BAR);
     if (tid == 0) {
@@ -629,7 +639,6 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
 
     // this CTA among every CTA of the pass stage (all slabs of a split cube)
     const int cta = a.sp.cta_base + bx + gx * (by + gy * bz);
-    const int ncta = a.sp.cta_total > 0 ? a.sp.cta_total : gx * gy * gz;
     if (W.s || W.t) {
         // the buffered window candidates join the global list (one atomic per vector)
         __syncthreads();
@@ -645,17 +654,11 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
                 if (cbase[v] + k < kCandCap) a.l1.cand[v][cbase[v] + k] = cbuf[v * L::CB + k];
             // and into the list's key histogram over the window, which the
             // finish then narrows without another pass over the candidates
-            // (values that overflowed the buffer are not counted: the finish
-            // then bins the list itself)
-            const bool on = v == 0 ? W.s : W.t;
-            if (on && a.l1.nh) {
-                const NarrowGeom ng = narrow_geom(__float_as_uint(v == 0 ? W.lo_s : W.lo_t),
-                                                  __float_as_uint(v == 0 ? W.hi_s : W.hi_t));
-                if (ng.ok) {
-                    unsigned* h = a.l1.nh + v * 3 * kNarrowBins;
-                    for (unsigned k = tid; k < n; k += L::NT) narrow_add(h, ng, __float_as_uint(cbuf[v * L::CB + k]));
-                    if (tid == 0 && n) atomicAdd(a.l1.nbinned + v, n);
-                }
+            unsigned* h = v == 0 ? W.nh_s : W.nh_t;
+            if (h) {
+                const NarrowGeom& ng = v == 0 ? W.ng_s : W.ng_t;
+                for (unsigned k = tid; k < n; k += L::NT) narrow_add(h, ng, __float_as_uint(cbuf[v * L::CB + k]));
+                if (tid == 0 && n) atomicAdd(a.l1.nbinned + v, n);
             }
         }
         if (W.hs || W.ht) {
@@ -710,103 +713,12 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
             }
         }
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) is_last = (atomicAdd(&a.sc->k1_ticket, 1u) == (unsigned)(ncta - 1));
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    // every CTA's partial counts and sums, both vectors and both statistics
-    // at once (four 16-byte loads per CTA, independent)
-    unsigned long long pn4[4] = {0, 0, 0, 0};
-    double ps4[4] = {0.0, 0.0, 0.0, 0.0};
-    if (W.s || W.t) {
-        const ulonglong2* n2 = reinterpret_cast<const ulonglong2*>(a.l1.k1_n);
-        const double2* s2 = reinterpret_cast<const double2*>(a.l1.k1_s);
-#pragma unroll 4
-        for (int k = tid; k < ncta; k += L::NT) {
-            const ulonglong2 na = __ldcg(n2 + 2 * k), nb = __ldcg(n2 + 2 * k + 1);
-            const double2 sa = __ldcg(s2 + 2 * k), sb = __ldcg(s2 + 2 * k + 1);
-            pn4[0] += na.x; pn4[1] += na.y; pn4[2] += nb.x; pn4[3] += nb.y;
-            ps4[0] += sa.x; ps4[1] += sa.y; ps4[2] += sb.x; ps4[3] += sb.y;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            pn4[q] = block_sum(pn4[q], red_u);
-            ps4[q] = block_sum(ps4[q], red_d);
-            if (tid == 0) { tail_n[q] = pn4[q]; tail_s[q] = ps4[q]; }
-        }
-        __syncthreads();
+    // what this pass counted, for the finishing launch that follows (every
+    // CTA agrees; the first writes it)
+    if (cta == 0 && tid == 0) {
+        a.sc->k1_win[0] = W.s; a.sc->k1_win[1] = W.t;
+        a.sc->k1_hist[0] = W.hs; a.sc->k1_hist[1] = W.ht;
     }
-    for (int v = 0; v < 2; ++v) {
-        L1Ctl& C = a.sc->ctl[v];
-        const double r = a.sc->radius[v];
-        const bool win = v == 0 ? W.s : W.t;
-        if (!(r > 0.0)) {
-            if (tid == 0) {
-                C.tau = __int_as_float(0x7f800000);
-                C.have_tau = 1;
-                C.need = NEED_NONE;
-                C.window_ok = 0;
-            }
-            continue;
-        }
-        if (!win) {
-            if (tid == 0) {
-                C.need = NEED_RADIX0; C.prefix = 0; C.n_above = 0; C.s_above = 0.0; C.exact_runs++;
-            }
-            continue;
-        }
-        const unsigned long long n = tail_n[v];
-        const double s = tail_s[v];
-        const unsigned m = __ldcg(&a.sc->acc[v].m);
-        const double tlo = C.theta_lo, thi = C.theta_hi;
-        double tau = 0.0;
-        WinInfo wi;
-        // the tile's shared memory below the histogram is idle now: a stage
-        // for the candidates and the narrowing scratch at its end
-        constexpr int kScr = 3 * kNarrowBins * 4;
-        const int miss = l1_window_finish((double)n, s, a.l1.cand[v], m, tlo, thi, r, &tau, red_d, red_u, &wi,
-                                          reinterpret_cast<float*>(sm), (L::OFF_HIST - kScr) / 4,
-                                          reinterpret_cast<unsigned*>(sm + L::OFF_HIST - kScr),
-                                          narrow_pre(a.l1, v, m));
-        narrow_clear(a.l1, v);
-        // after a miss, the histogram (when on) brackets the root for one
-        // retry pass over the bracket
-        const bool hist_v = v == 0 ? W.hs : W.ht;
-        int hist_hit = 0;
-        float h_lo = 0.f, h_hi = 0.f;
-        double h_m = 0.0;
-        if (miss && hist_v) {
-            const unsigned long long hn = tail_n[2 + v];
-            const double hs = tail_s[2 + v];
-            hist_hit = l1_hist_bracket(a.l1.khist + v * kK1Bins, v == 0 ? W.hb_s : W.hb_t, (double)hn, hs, r,
-                                       (double)kHistSample, &h_lo, &h_hi, &h_m, &sh_flag,
-                                       reinterpret_cast<unsigned*>(sm + L::OFF_HIST));
-        }
-        if (hist_v) {
-            __syncthreads();
-            for (int k = tid; k < kK1Bins; k += L::NT) a.l1.khist[v * kK1Bins + k] = 0u;
-        }
-        if (tid == 0) {
-            if (!miss) {
-                l1_record_tau(C, tau, (double)min(m, kCandCap), thi - tlo, true);
-                C.hits++;
-                if (C.hist_left > 0) C.hist_left--;
-            } else if (hist_hit) {
-                C.prefix = 0; C.n_above = 0; C.s_above = 0.0;
-                C.need = NEED_WINDOW;
-                C.g_lo = h_lo;
-                C.g_hi = h_hi;
-                C.hist_left = kHistPasses;
-            } else {
-                l1_after_miss(C, miss, wi, (double)n, m, tlo, thi);
-            }
-            a.sc->acc[v].m = 0;
-        }
-        __syncthreads();
-    }
-    if (tid == 0) a.sc->k1_ticket = 0;
 }
 
 __global__ void __launch_bounds__(512, 1) k1_tma(const __grid_constant__ K1Maps maps, const K1TArgs a) {
@@ -834,12 +746,21 @@ __device__ __forceinline__ int batch_cube_of(const int* start, int n, int blk) {
 
 __global__ void __launch_bounds__(512, 1) k1_tma_batch(const __grid_constant__ K1BatchTab t) {
     const int c = batch_cube_of(t.start, t.n, blockIdx.x);
-    const K1TArgs& a = t.args[c];
+    // the cube's arguments by value: the table is indexed by a run-time
+    // cube, so each field is loaded once instead of at each use
+    const K1TArgs a = t.args[c];
     if (__ldcg(&a.sc->done)) return;        // this cube has stopped
     const int gx = t.gx[c], gy = t.gy[c], gz = t.gz[c];
     const int l = blockIdx.x - t.start[c];
     const int bx = l % gx, by = (l / gx) % gy, bz = l / (gx * gy);
-    k1_run(*t.maps[c], a, bx, by, bz, gx, gy, gz);
+    const K1Maps* maps = t.maps[c];
+    if (threadIdx.x == Lay::PRODUCER) {
+        // the cube's tensor maps sit in global memory (the copies' descriptors)
+        tma_prefetch_map(&maps->y1); tma_prefetch_map(&maps->y2); tma_prefetch_map(&maps->w1);
+        tma_prefetch_map(&maps->w2); tma_prefetch_map(&maps->u); tma_prefetch_map(&maps->q);
+        tma_prefetch_map(&maps->s); tma_prefetch_map(&maps->t); tma_prefetch_map(&maps->y3);
+    }
+    k1_run(*maps, a, bx, by, bz, gx, gy, gz);
 }
 
 // Bands per CTA.  One CTA runs per SM, so a launch of U CTAs on S SMs takes
