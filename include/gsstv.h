@@ -93,6 +93,9 @@ typedef struct gsstv_stats {
     double  last_l2_scale;     /* min(1, eps / ||y4'/gamma_y4 - v||) (Eq. 23) */
     int64_t tau_retry_hits;    /* l1 thresholds found by one retry pass over a
                                   window placed after a miss                  */
+    int64_t search_passes;     /* graph-launched passes whose threshold search
+                                  launches ran (the rest skip them: K1's
+                                  window found both thresholds)               */
 } gsstv_stats;
 
 /* Device views of the full state (float32, each a (N3,N1,N2) cube or a stack

@@ -46,7 +46,7 @@ class GsstvStats(ctypes.Structure):
         ("iterations", c_int64), ("tau_window_hits", c_int64), ("tau_exact_runs", c_int64),
         ("k1_ms", c_double), ("k1_launches", c_int64),
         ("last_rel_change", c_double), ("last_tau_s", c_double), ("last_tau_t", c_double),
-        ("last_l2_scale", c_double), ("tau_retry_hits", c_int64),
+        ("last_l2_scale", c_double), ("tau_retry_hits", c_int64), ("search_passes", c_int64),
     ]
 
 

@@ -30,6 +30,7 @@ struct gsstv_handle {
     gsstv_params p{};
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;   // private stream used only to capture graphs
+    cudaStream_t cap2 = nullptr;  // and one for the bodies of conditional graph nodes
     int esz = 4;
     void *u[2]{}, *s[2]{}, *t[2]{}, *y3[2]{}, *q[2]{};
     void *w1[2]{}, *w2[2]{}, *y1[2]{}, *y2[2]{};
@@ -50,6 +51,12 @@ struct gsstv_handle {
     int timing = 0;
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
+    // graphs with K1 between timing events: one per parity and slot of 2 x len
+    // events of the pool (kept, like the untimed graphs, until the launch
+    // shape changes)
+    static constexpr int kTimedSlots = 16;
+    cudaGraphExec_t timed_exec[2][kTimedSlots]{};
+    int timed_len = 0;
     gsstv_stats stats{};
     int64_t bytes = 0;
     std::vector<void*> allocs;
@@ -96,10 +103,14 @@ int dalloc(gsstv_handle* h, void** out, size_t bytes) {
 void free_all(gsstv_handle* h) {
     for (int k = 0; k < 2; ++k)
         if (h->gexec[k]) { cudaGraphExecDestroy(h->gexec[k]); h->gexec[k] = nullptr; }
+    cudaStreamSynchronize(h->st);
+    for (auto& row : h->timed_exec)
+        for (cudaGraphExec_t& x : row)
+            if (x) { cudaGraphExecDestroy(x); x = nullptr; }
     for (cudaEvent_t e : h->ev) if (e) cudaEventDestroy(e);
     h->ev.clear();
-    cudaStreamSynchronize(h->st);
     if (h->cap) { cudaStreamDestroy(h->cap); h->cap = nullptr; }
+    if (h->cap2) { cudaStreamDestroy(h->cap2); h->cap2 = nullptr; }
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
 }
@@ -108,6 +119,11 @@ void destroy_graphs(gsstv_handle* h) {
     for (int k = 0; k < 2; ++k)
         if (h->gexec[k]) { cudaGraphExecDestroy(h->gexec[k]); h->gexec[k] = nullptr; }
     h->graph_len = 0;
+    if (h->timed_len) cudaStreamSynchronize(h->st);
+    for (auto& row : h->timed_exec)
+        for (cudaGraphExec_t& x : row)
+            if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+    h->timed_len = 0;
 }
 
 IterBufs bufs(const gsstv_handle* h, int par) {
@@ -143,14 +159,54 @@ IterParams iparams(const gsstv_handle* h, int par) {
 
 int map_launch(int rc) { return rc == 0 ? GSSTV_OK : rc == -1 ? GSSTV_ERR_ARG : GSSTV_ERR_CUDA; }
 
-// One iteration from parity `par` (reads buffers par, writes par ^ 1) on `st`.
-int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
+// While `st` is being captured into a graph: the launches that body(stream)
+// enqueues become the body of a conditional node, run only when the gate
+// kernel launched just before it finds that one of the n cubes with scalars
+// sc[] needs a threshold search (after K1's window finish, most passes need
+// none, and the seven search launches would each start and return at once).
+// The body is captured from the side stream `side`.
+template <typename F>
+int capture_if_search(cudaStream_t st, cudaStream_t side, Scal* const* sc, int n, F&& body) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    TRY(cuda_rc(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd)));
+    if (cs != cudaStreamCaptureStatusActive) return GSSTV_ERR_INTERNAL;
+    cudaGraphConditionalHandle cond = 0;
+    TRY(cuda_rc(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault)));
+    TRY(map_launch(launch_search_gate(sc, n, cond, st)));
+    TRY(cuda_rc(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd)));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    TRY(cuda_rc(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np)));
+    TRY(cuda_rc(cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal)));
+    const int rc = body(side);
+    cudaGraph_t body_graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(side, &body_graph);
+    TRY(rc);
+    TRY(cuda_rc(e));
+    TRY(cuda_rc(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)));
+    return GSSTV_OK;
+}
+
+// One iteration from parity `par` (reads buffers par, writes par ^ 1) on `st`;
+// in_graph: `st` is being captured (the search launches then sit behind a
+// conditional node).
+int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st, bool in_graph = false) {
     const IterBufs b = bufs(h, par);
     const IterParams ip = iparams(h, par);
     const int sto = h->p.storage;
     if (timed) {
         if (h->ev_used + 2 > (int)h->ev.size()) return GSSTV_ERR_INTERNAL;
-        TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used], st)));
+        // inside a capture only an external record becomes a graph node
+        TRY(cuda_rc(in_graph ? cudaEventRecordWithFlags(h->ev[h->ev_used], st, cudaEventRecordExternal)
+                             : cudaEventRecord(h->ev[h->ev_used], st)));
     }
     const SlabPart whole = whole_cube(h->g);
     if (h->k1_variant == 1)
@@ -158,7 +214,8 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
     else
         TRY(map_launch(launch_k1(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, st)));
     if (timed) {
-        TRY(cuda_rc(cudaEventRecord(h->ev[h->ev_used + 1], st)));
+        TRY(cuda_rc(in_graph ? cudaEventRecordWithFlags(h->ev[h->ev_used + 1], st, cudaEventRecordExternal)
+                             : cudaEventRecord(h->ev[h->ev_used + 1], st)));
         h->ev_used += 2;
     }
     // the TMA-fed K1 leaves its window's finish to a launch of its own (the
@@ -166,13 +223,20 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
     if (h->k1_variant == 1)
         TRY(map_launch(launch_search_finish(2, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
                                             k1_tma_grid(h->g, whole, h->k1_chunk), st)));
-    TRY(map_launch(launch_window(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, whole, st)));
-    TRY(map_launch(launch_search_finish(0, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
-                                        window_grid(h->g, whole, h->k1_ctas), st)));
-    for (int level = 0; level < 3; ++level)
-        TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, whole, st)));
-    TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, whole, st)));
-    TRY(map_launch(launch_search_finish(1, h->sc, h->l1, 2, nullptr, nullptr, 0, st)));
+    auto search = [&](cudaStream_t s) -> int {
+        TRY(map_launch(launch_window(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, whole, s)));
+        TRY(map_launch(launch_search_finish(0, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
+                                            window_grid(h->g, whole, h->k1_ctas), s)));
+        for (int level = 0; level < 3; ++level)
+            TRY(map_launch(launch_fallback(sto, level, h->g, b, ip, h->sc, h->l1, whole, s)));
+        TRY(map_launch(launch_gather(sto, h->g, b, ip, h->sc, h->l1, whole, s)));
+        TRY(map_launch(launch_search_finish(1, h->sc, h->l1, 2, nullptr, nullptr, 0, s)));
+        return GSSTV_OK;
+    };
+    if (in_graph)
+        TRY(capture_if_search(st, h->cap2, &h->sc, 1, search));
+    else
+        TRY(search(st));
     TRY(map_launch(launch_k2(sto, h->g, b, ip, h->sc, h->k2_part, h->k2_cap, whole, st)));
     return GSSTV_OK;
 }
@@ -180,22 +244,25 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st) {
 // Captures `len` iterations starting at parity `par` on the private capture
 // stream (the caller's stream may be the legacy default stream, which cannot
 // be captured); the executable graph is launched on the caller's stream.
-int build_graph(gsstv_handle* h, int par, int len) {
+// timed: each iteration's K1 between two of the handle's timing events (a
+// graph built for one launch, since its events are read afterwards).
+int build_graph_exec(gsstv_handle* h, int par, int len, bool timed, cudaGraphExec_t* out) {
     cudaGraph_t graph = nullptr;
     TRY(cuda_rc(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal)));
     int rc = GSSTV_OK;
     int p = par;
     for (int k = 0; k < len && rc == GSSTV_OK; ++k) {
-        rc = enqueue_iteration(h, p, false, h->cap);
+        rc = enqueue_iteration(h, p, timed, h->cap, true);
         p ^= 1;
     }
     cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
     if (rc != GSSTV_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
     if (e != cudaSuccess) return GSSTV_ERR_CUDA;
-    e = cudaGraphInstantiate(&h->gexec[par], graph, 0);
+    e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     return cuda_rc(e);
 }
+int build_graph(gsstv_handle* h, int par, int len) { return build_graph_exec(h, par, len, false, &h->gexec[par]); }
 
 int flush_timing(gsstv_handle* h) {
     if (h->ev_used == 0) return GSSTV_OK;
@@ -219,6 +286,20 @@ int run_block(gsstv_handle* h, int n) {
             if (!h->gexec[h->parity]) TRY(build_graph(h, h->parity, G));
             h->graph_len = G;
             TRY(cuda_rc(cudaGraphLaunch(h->gexec[h->parity], h->st)));
+            n -= G;
+            h->stats.iterations += G;
+        } else if (h->timing && G > 0 && n >= G && 2 * G * gsstv_handle::kTimedSlots <= (int)h->ev.size()) {
+            // the same graphs with K1 between timing events: the graph of
+            // slot k records events [2 G k, 2 G (k + 1)) of the pool, which
+            // are read (flush_timing) before the slot is launched again
+            if (h->ev_used % (2 * G) != 0 || h->ev_used + 2 * G > 2 * G * gsstv_handle::kTimedSlots)
+                TRY(flush_timing(h));
+            if (h->timed_len != G) destroy_graphs(h);
+            h->timed_len = G;
+            cudaGraphExec_t& x = h->timed_exec[h->parity][h->ev_used / (2 * G)];
+            if (!x) TRY(build_graph_exec(h, h->parity, G, true, &x));     // advances ev_used by 2 G
+            else h->ev_used += 2 * G;
+            TRY(cuda_rc(cudaGraphLaunch(x, h->st)));
             n -= G;
             h->stats.iterations += G;
         } else {
@@ -311,6 +392,10 @@ int gsstv_create(gsstv_handle** out, int n1, int n2, int n3, const gsstv_params*
     }
     if (rc == GSSTV_OK && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
         h->cap = nullptr;
+        rc = GSSTV_ERR_CUDA;
+    }
+    if (rc == GSSTV_OK && cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking) != cudaSuccess) {
+        h->cap2 = nullptr;
         rc = GSSTV_ERR_CUDA;
     }
     if (rc == GSSTV_OK) rc = dalloc(h, (void**)&h->v, (size_t)h->g.cube * sizeof(float));
@@ -568,6 +653,7 @@ int gsstv_get_stats(gsstv_handle* h, gsstv_stats* out) {
     out->tau_window_hits = s.ctl[0].hits + s.ctl[1].hits;
     out->tau_exact_runs = s.ctl[0].exact_runs + s.ctl[1].exact_runs;
     out->tau_retry_hits = s.ctl[0].retry_hits + s.ctl[1].retry_hits;
+    out->search_passes = s.gate_opens;
     return GSSTV_OK;
 }
 
@@ -578,6 +664,7 @@ int gsstv_reset_stats(gsstv_handle* h) {
     Scal s;
     TRY(read_scalars(h, &s));
     for (int v = 0; v < 2; ++v) { s.ctl[v].hits = 0; s.ctl[v].exact_runs = 0; s.ctl[v].retry_hits = 0; }
+    s.gate_opens = 0;
     return upload_scalars(h, s);
 }
 
@@ -585,6 +672,18 @@ int gsstv_set_timing(gsstv_handle* h, int on) {
     if (!h) return GSSTV_ERR_ARG;
     TRY(flush_timing(h));
     h->timing = on ? 1 : 0;
+    // build the timed graphs of the current parity now, so that timed passes
+    // do not wait for them
+    const int G = h->p.graph_iters > 0 ? ((h->p.graph_iters + 1) / 2) * 2 : 0;
+    if (on && G > 0 && 2 * G * gsstv_handle::kTimedSlots <= (int)h->ev.size()) {
+        if (h->timed_len != G) destroy_graphs(h);
+        h->timed_len = G;
+        for (int k = 0; k < gsstv_handle::kTimedSlots; ++k) {
+            h->ev_used = 2 * G * k;
+            if (!h->timed_exec[h->parity][k]) TRY(build_graph_exec(h, h->parity, G, true, &h->timed_exec[h->parity][k]));
+        }
+        h->ev_used = 0;
+    }
     return GSSTV_OK;
 }
 
@@ -773,6 +872,7 @@ struct gsstv_batch {
     int* live = nullptr;           // device: cubes still iterating
     int* live_host = nullptr;      // page-locked copy
     cudaStream_t cap = nullptr;    // private capture stream
+    cudaStream_t cap2 = nullptr;   // and one for the bodies of conditional graph nodes
     cudaGraphExec_t gexec = nullptr;
     int graph_len = 0;
     std::vector<int> graph_chunks;  // the cubes' K1 band runs the graph was built with
@@ -784,6 +884,7 @@ int gsstv_batch_destroy(gsstv_batch* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->caller) cudaStreamSynchronize(b->caller);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->cap2) cudaStreamDestroy(b->cap2);
     if (b->dmaps) cudaFree(b->dmaps);
     if (b->live) cudaFree(b->live);
     if (b->live_host) cudaFreeHost(b->live_host);
@@ -850,6 +951,10 @@ int gsstv_batch_create(gsstv_batch** out, int ncubes, const int* n1, const int* 
             b->cap = nullptr;
             rc = GSSTV_ERR_CUDA;
         }
+        if (rc == GSSTV_OK && cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking) != cudaSuccess) {
+            b->cap2 = nullptr;
+            rc = GSSTV_ERR_CUDA;
+        }
         for (int c = 0; c < ncubes && rc == GSSTV_OK; ++c)
             rc = cuda_rc(cudaMemcpy(b->dmaps + 2 * c, b->h[c]->maps, 2 * sizeof(K1Maps), cudaMemcpyHostToDevice));
     }
@@ -888,11 +993,18 @@ int batch_enqueue(gsstv_batch* b, const std::vector<int>& set, int par, cudaStre
     }
     TRY(map_launch(launch_k1_batch(cubes, nc, st)));
     TRY(map_launch(launch_finish_batch(cubes, nc, 2, st)));
-    TRY(map_launch(launch_window_batch(cubes, nc, st)));
-    TRY(map_launch(launch_finish_batch(cubes, nc, 0, st)));
-    for (int level = 0; level < 3; ++level) TRY(map_launch(launch_radix_batch(cubes, nc, level, st)));
-    TRY(map_launch(launch_gather_batch(cubes, nc, st)));
-    TRY(map_launch(launch_finish_batch(cubes, nc, 1, st)));
+    // the search launches behind a conditional node (the fused solve is
+    // always captured)
+    Scal* scs[kBatchMax];
+    for (int k = 0; k < nc; ++k) scs[k] = cubes[k].sc;
+    TRY(capture_if_search(st, b->cap2, scs, nc, [&](cudaStream_t q) -> int {
+        TRY(map_launch(launch_window_batch(cubes, nc, q)));
+        TRY(map_launch(launch_finish_batch(cubes, nc, 0, q)));
+        for (int level = 0; level < 3; ++level) TRY(map_launch(launch_radix_batch(cubes, nc, level, q)));
+        TRY(map_launch(launch_gather_batch(cubes, nc, q)));
+        TRY(map_launch(launch_finish_batch(cubes, nc, 1, q)));
+        return GSSTV_OK;
+    }));
     TRY(map_launch(launch_k2_batch(cubes, nc, st)));
     return GSSTV_OK;
 }
@@ -1084,6 +1196,7 @@ struct gsstv_slabs {
     gsstv_params p{};
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t cap2 = nullptr;
     std::vector<gsstv_handle*> h;        // slab storage: bands [L0, L0 + h->g.n3) of the cube
     std::vector<int> B0, B1, L0;         // owned bands [B0, B1), first stored band L0
     std::vector<SlabPart> k1p, winp, radp, gatp, k2p;
@@ -1117,6 +1230,7 @@ void slabs_free(gsstv_slabs* G) {
         if (G->gexec[k]) { cudaGraphExecDestroy(G->gexec[k]); G->gexec[k] = nullptr; }
     if (G->st) cudaStreamSynchronize(G->st);
     if (G->cap) { cudaStreamDestroy(G->cap); G->cap = nullptr; }
+    if (G->cap2) { cudaStreamDestroy(G->cap2); G->cap2 = nullptr; }
     for (void* q : G->allocs) cudaFree(q);
     G->allocs.clear();
     for (gsstv_handle* x : G->h) gsstv_destroy(x);
@@ -1135,7 +1249,7 @@ void number_stage(std::vector<SlabPart>& parts, const std::vector<int>& grids) {
 }
 
 // One pass from parity `par` on `st`: every stage on every slab, then the halos.
-int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st) {
+int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st, bool in_graph = false) {
     const int S = G->S;
     const IterParams ip = iparams(G->h[0], par);
     for (int s = 0; s < S; ++s) {
@@ -1144,21 +1258,30 @@ int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st) {
                                      G->k1_chunk[s], G->k1p[s], st)));
     }
     TRY(map_launch(launch_search_finish(2, G->sc, G->l1, 2, G->l1.k1_n, G->l1.k1_s, G->k1p[0].cta_total, st)));
-    for (int s = 0; s < S; ++s) {
-        gsstv_handle* x = G->h[s];
-        TRY(map_launch(launch_window(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->win_cap, G->winp[s], st)));
-    }
-    TRY(map_launch(launch_search_finish(0, G->sc, G->l1, 2, G->l1.k1_n, G->l1.k1_s, G->winp[0].cta_total, st)));
-    for (int level = 0; level < 3; ++level)
+    auto search = [&](cudaStream_t q) -> int {
         for (int s = 0; s < S; ++s) {
             gsstv_handle* x = G->h[s];
-            TRY(map_launch(launch_fallback(GSSTV_FP32, level, x->g, bufs(x, par), ip, G->sc, G->l1, G->radp[s], st)));
+            TRY(map_launch(launch_window(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->win_cap, G->winp[s],
+                                         q)));
         }
-    for (int s = 0; s < S; ++s) {
-        gsstv_handle* x = G->h[s];
-        TRY(map_launch(launch_gather(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->gatp[s], st)));
-    }
-    TRY(map_launch(launch_search_finish(1, G->sc, G->l1, 2, nullptr, nullptr, 0, st)));
+        TRY(map_launch(launch_search_finish(0, G->sc, G->l1, 2, G->l1.k1_n, G->l1.k1_s, G->winp[0].cta_total, q)));
+        for (int level = 0; level < 3; ++level)
+            for (int s = 0; s < S; ++s) {
+                gsstv_handle* x = G->h[s];
+                TRY(map_launch(launch_fallback(GSSTV_FP32, level, x->g, bufs(x, par), ip, G->sc, G->l1, G->radp[s],
+                                               q)));
+            }
+        for (int s = 0; s < S; ++s) {
+            gsstv_handle* x = G->h[s];
+            TRY(map_launch(launch_gather(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->l1, G->gatp[s], q)));
+        }
+        TRY(map_launch(launch_search_finish(1, G->sc, G->l1, 2, nullptr, nullptr, 0, q)));
+        return GSSTV_OK;
+    };
+    if (in_graph)
+        TRY(capture_if_search(st, G->cap2, &G->sc, 1, search));
+    else
+        TRY(search(st));
     for (int s = 0; s < S; ++s) {
         gsstv_handle* x = G->h[s];
         TRY(map_launch(launch_k2(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->k2_part, G->k2_cap, G->k2p[s], st)));
@@ -1194,7 +1317,7 @@ int slabs_build_graph(gsstv_slabs* G, int par, int len) {
     int rc = GSSTV_OK;
     int q = par;
     for (int k = 0; k < len && rc == GSSTV_OK; ++k) {
-        rc = slabs_enqueue(G, q, G->cap);
+        rc = slabs_enqueue(G, q, G->cap, true);
         q ^= 1;
     }
     cudaError_t e = cudaStreamEndCapture(G->cap, &graph);
@@ -1294,6 +1417,10 @@ int gsstv_slabs_create(gsstv_slabs** out, int n1, int n2, int n3, int nslabs, co
         G->cap = nullptr;
         rc = GSSTV_ERR_CUDA;
     }
+    if (rc == GSSTV_OK && cudaStreamCreateWithFlags(&G->cap2, cudaStreamNonBlocking) != cudaSuccess) {
+        G->cap2 = nullptr;
+        rc = GSSTV_ERR_CUDA;
+    }
     if (rc == GSSTV_OK) {
         // each stage's launches, numbered across the slabs
         std::vector<int> gk1, gw, gr, gg, gk2;
@@ -1391,6 +1518,7 @@ int gsstv_slabs_iterate(gsstv_slabs* G, int n, int* iters_done) {
     G->stats.tau_window_hits = s.ctl[0].hits + s.ctl[1].hits;
     G->stats.tau_exact_runs = s.ctl[0].exact_runs + s.ctl[1].exact_runs;
     G->stats.tau_retry_hits = s.ctl[0].retry_hits + s.ctl[1].retry_hits;
+    G->stats.search_passes = s.gate_opens;
     if (iters_done) *iters_done = done;
     return GSSTV_OK;
 }

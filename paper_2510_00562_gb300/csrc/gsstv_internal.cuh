@@ -161,12 +161,13 @@ struct Scal {
     // what the fused pass (TMA-fed K1) counted for vector v, for the finish
     // that follows it: its window statistics and candidates, its histogram
     int k1_win[2], k1_hist[2];
+    long long gate_opens;      // passes whose threshold search launches ran (graphs)
 };
 
 constexpr int kHistBins = 2048;        // radix histogram bins per vector
 constexpr unsigned kCandCap = 1u << 20; // candidate capacity per vector
 constexpr int kNarrowBins = 2048;        // bins of one narrowing round of a candidate list
-constexpr double kCandTarget = 65536.0;  // K1's window is sized for at most about this many candidates
+constexpr double kCandTarget = 393216.0;  // K1's window is sized for at most about this many candidates
 constexpr double kRetryTarget = 262144.0; // a retry window after a miss: at most about this many
 constexpr unsigned kGatherMax = 1u << 16; // a radix bracket this small is gathered, a larger one refined
 // K1's histogram of |x| near the predicted threshold: 1024 bins of 1/256
@@ -437,6 +438,9 @@ int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p
 // The finish of the retry window (mode 0; parts: CTAs of the window pass(es),
 // their partial sums in pn / ps) or of the gathered radix bracket (mode 1),
 // for every vector that needs it: one launch after the pass(es) it finishes.
+// Sets `cond` (a graph conditional handle) to whether any of the n cubes
+// whose scalars are sc[] needs a threshold search after K1's finish.
+int launch_search_gate(Scal* const* sc, int n, cudaGraphConditionalHandle cond, cudaStream_t st);
 int launch_search_finish(int mode, Scal* sc, const L1Work& w, int nvec, const unsigned long long* pn,
                          const double* ps, int parts, cudaStream_t st);
 int k2_grid_ctas(const Geom& g);

@@ -1095,6 +1095,36 @@ int launch_gather_batch(const BatchCube* cubes, int n, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+// Whether any cube still needs a threshold search after K1's finish: sets the
+// condition of the graph node that holds the search launches (one thread, so
+// that no two calls race).
+struct GateArgs {
+    Scal* sc[kBatchMax];
+    int n;
+    cudaGraphConditionalHandle cond;
+};
+__global__ void k_search_gate(const __grid_constant__ GateArgs g) {
+    if (threadIdx.x != 0) return;
+    unsigned need = 0u;
+    for (int c = 0; c < g.n; ++c) {
+        const Scal* s = g.sc[c];
+        if (__ldcg(&s->done)) continue;
+        if (__ldcg(&s->ctl[0].need) != NEED_NONE || __ldcg(&s->ctl[1].need) != NEED_NONE) need = 1u;
+    }
+    if (need) g.sc[0]->gate_opens++;
+    cudaGraphSetConditional(g.cond, need);
+}
+
+int launch_search_gate(Scal* const* sc, int n, cudaGraphConditionalHandle cond, cudaStream_t st) {
+    if (n < 1 || n > kBatchMax) return -1;
+    GateArgs g{};
+    for (int c = 0; c < n; ++c) g.sc[c] = sc[c];
+    g.n = n;
+    g.cond = cond;
+    k_search_gate<<<1, 32, 0, st>>>(g);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st) {
     SearchBatchTab t{};
     if (search_table(cubes, n, t, [](const BatchCube&, const SlabPart&) { return 1; }) < 0) return -1;
