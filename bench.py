@@ -316,15 +316,15 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-GRAPH_PASSES = 16            # passes per CUDA graph (graph_iters)
+GRAPH_PASSES = 16            # passes per CUDA graph (graph_iters), the solver's default
 
 
-def gpu_launches(steps, search_passes):
-    """Kernels launched in `steps` timed passes: whole graphs of GRAPH_PASSES
+def gpu_launches(steps, search_passes, graph_passes=GRAPH_PASSES):
+    """Kernels launched in `steps` timed passes: whole graphs of graph_passes
     passes launch K1, its window finish, the search gate and K2, plus the seven
     search launches in the passes whose gate opened (search_passes); the
     remaining passes run eagerly, all ten launches each."""
-    in_graphs = (steps // GRAPH_PASSES) * GRAPH_PASSES
+    in_graphs = (steps // graph_passes) * graph_passes if graph_passes > 0 else 0
     return 4 * in_graphs + 7 * search_passes + 10 * (steps - in_graphs)
 
 
@@ -345,7 +345,7 @@ def run_gpu(args):
     pb = synth.make_problem(n1, n2, n3, seed=rank, noise=synth.NoiseSpec(**NOISE))
     esz = 4 if args.storage == "fp32" else 2
     p = make_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03,
-                    max_iter=args.steps, storage=args.storage, graph_iters=GRAPH_PASSES)
+                    max_iter=args.steps, storage=args.storage, graph_iters=args.graph_passes)
     stream = torch.cuda.current_stream()
     sol = GeoSSTVSolver(n1, n2, n3, p, stream=stream)
     v_dev = torch.from_numpy(pb["v"]).cuda()
@@ -436,7 +436,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 3 * 4 * nvox / args.steps,
                 "note": "one gsstv_solve_host call of `steps` iterations: pinned H2D of v, "
                         "state reset, iterations, D2H of u, s, t"},
-        "gpu_launches": gpu_launches(args.steps, st["search_passes"]),
+        "gpu_launches": gpu_launches(args.steps, st["search_passes"], args.graph_passes),
         "quality": quality,
     }
     if pf:
@@ -928,6 +928,8 @@ def main(argv=None):
     ap.add_argument("--grad-ckpt", type=int, default=20, help="passes between checkpoints")
     ap.add_argument("--slabs", type=int, nargs="*", default=None, metavar="S",
                     help="run only the band-slab measurement with these slab counts")
+    ap.add_argument("--graph-passes", type=int, default=GRAPH_PASSES,
+                    help="passes per CUDA graph (0: every launch from the host, e.g. for a per-kernel launch list)")
     ap.add_argument("--shape", default="512x512x224",
                     help="N1xN2xN3; anything but the default is a profiling case, not a bench line")
     args = ap.parse_args(argv)
