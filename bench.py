@@ -431,7 +431,7 @@ def run_gpu(args):
             "floor_gbs": FLOOR_WORDS_FP32 * 4 * nvox * args.steps / (ms_max * 1e-3) / 1e9 if esz == 4 else None,
         },
         "tau_search": {"window_hits": st["tau_window_hits"], "retry_hits": st["tau_retry_hits"],
-                       "exact_runs": st["tau_exact_runs"]},
+                       "exact_runs": st["tau_exact_runs"], "search_passes": st["search_passes"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * nvox / args.steps,
                 "d2h_bytes_per_step": 3 * 4 * nvox / args.steps,
                 "note": "one gsstv_solve_host call of `steps` iterations: pinned H2D of v, "

@@ -30,26 +30,33 @@ struct WinInfo {
     double n_lo = 0.0;     // count of |x| > theta_lo
 };
 
-// Calls f(x, k) for every candidate x = cand[k], k < m, with 16 values in
-// flight per thread (four 16-byte loads): one CTA walking a long candidate
-// list is bound by the latency of its loads, not by their bandwidth.  cand
-// must be 16-byte aligned (every candidate buffer starts on a 256-byte
-// boundary).
+// Calls f(x, k) for every candidate x = cand[k], k < m, with kCandBatch
+// 16-byte loads in flight per thread (then four, then one): one CTA walking a
+// long candidate list is bound by the latency of its loads, not by their
+// bandwidth.  cand must be 16-byte aligned (every candidate buffer starts on
+// a 256-byte boundary).
+constexpr int kCandBatch = 4;
+template <int B, typename F>
+__device__ __forceinline__ unsigned candidate_batches(const float4* c4, unsigned k, unsigned m4, unsigned nt, F& f) {
+    for (; k + (B - 1u) * nt < m4; k += B * nt) {
+        float4 q[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) q[j] = __ldcg(c4 + k + j * nt);
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const unsigned b = 4u * (k + j * nt);
+            f(q[j].x, b); f(q[j].y, b + 1u); f(q[j].z, b + 2u); f(q[j].w, b + 3u);
+        }
+    }
+    return k;
+}
 template <typename F>
 __device__ __forceinline__ void for_each_candidate(const float* cand, unsigned m, F&& f) {
     const unsigned nt = blockDim.x, m4 = m / 4u;
     const float4* c4 = reinterpret_cast<const float4*>(cand);
     unsigned k = threadIdx.x;
-    for (; k + 3u * nt < m4; k += 4u * nt) {
-        float4 q[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) q[j] = __ldcg(c4 + k + j * nt);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const unsigned b = 4u * (k + j * nt);
-            f(q[j].x, b); f(q[j].y, b + 1u); f(q[j].z, b + 2u); f(q[j].w, b + 3u);
-        }
-    }
+    k = candidate_batches<kCandBatch>(c4, k, m4, nt, f);
+    if (kCandBatch > 4) k = candidate_batches<4>(c4, k, m4, nt, f);
     for (; k < m4; k += nt) {
         const float4 q = __ldcg(c4 + k);
         f(q.x, 4u * k); f(q.y, 4u * k + 1u); f(q.z, 4u * k + 2u); f(q.w, 4u * k + 3u);

@@ -229,7 +229,7 @@ __device__ __forceinline__ void k2_body(const K2Args<T>& a, const int bid, const
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k2_light(const K2Args<T> a) {
+__global__ void __launch_bounds__(NT, 3) k2_light(const K2Args<T> a) {
     k2_body(a, blockIdx.x, gridDim.x);
 }
 
@@ -939,7 +939,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish_batch(const __grid_co
     if (__ldcg(&q.a.sc->done)) return;
     finish_body(q.a, mode, q.pn, q.ps, q.parts, blockIdx.x & 1);
 }
-__global__ void __launch_bounds__(NT) k2_batch(const __grid_constant__ K2BatchTab t) {
+__global__ void __launch_bounds__(NT, 3) k2_batch(const __grid_constant__ K2BatchTab t) {
     const int c = batch_cube_of(t.start, t.n, blockIdx.x);
     // by value: the table is indexed by a run-time cube, so each field is
     // loaded once instead of at each use
