@@ -469,7 +469,12 @@ int gsstv_load_observation(gsstv_handle* h, const float* d_v) {
 int gsstv_reset_state(gsstv_handle* h) {
     if (!h) return GSSTV_ERR_ARG;
     const size_t cb = (size_t)h->g.cube * h->esz;
-    for (int k = 0; k < 2; ++k) {
+    // the standard start in the parity-0 buffers, which the first pass reads;
+    // it writes every voxel of the parity-1 buffers before any pass reads
+    // them (their padding columns stay zero from the allocation: the passes
+    // write zeros there), so those are not cleared
+    {
+        const int k = 0;
         void* one[] = {h->u[k], h->s[k], h->t[k], h->y3[k], h->q[k]};
         for (void* pp : one) TRY(cuda_rc(cudaMemsetAsync(pp, 0, cb, h->st)));
         TRY(cuda_rc(cudaMemsetAsync(h->w1[k], 0, 6 * cb, h->st)));
@@ -559,7 +564,11 @@ int gsstv_solve_host(gsstv_handle* h, const float* h_v, float* h_u, float* h_s, 
     if (!h || !h_v || !h_u) return GSSTV_ERR_ARG;
     const Geom& g = h->g;
     const size_t w = (size_t)g.n2 * 4, dp = (size_t)g.p2 * 4, rows = (size_t)g.n3 * g.n1;
-    TRY(cuda_rc(cudaMemcpy2DAsync(h->v, dp, h_v, w, w, rows, cudaMemcpyHostToDevice, h->st)));
+    // rows without padding (N2 a multiple of 8) copy as one block
+    if (dp == w)
+        TRY(cuda_rc(cudaMemcpyAsync(h->v, h_v, w * rows, cudaMemcpyHostToDevice, h->st)));
+    else
+        TRY(cuda_rc(cudaMemcpy2DAsync(h->v, dp, h_v, w, w, rows, cudaMemcpyHostToDevice, h->st)));
     TRY(gsstv_reset_state(h));
     TRY(gsstv_iterate(h, h->p.max_iter, iters_done));
     const int par = h->parity;
@@ -572,7 +581,9 @@ int gsstv_solve_host(gsstv_handle* h, const float* h_v, float* h_u, float* h_s, 
     }
     for (int k = 0; k < 3; ++k) {
         if (!dst[k]) continue;
-        if (h->p.storage == GSSTV_FP32) {
+        if (h->p.storage == GSSTV_FP32 && dp == w) {
+            TRY(cuda_rc(cudaMemcpyAsync(dst[k], src[k], w * rows, cudaMemcpyDeviceToHost, h->st)));
+        } else if (h->p.storage == GSSTV_FP32) {
             TRY(cuda_rc(cudaMemcpy2DAsync(dst[k], w, src[k], dp, w, rows, cudaMemcpyDeviceToHost, h->st)));
         } else {
             TRY(map_launch(launch_unpack(h->p.storage, src[k], h->tmp, g, 1, h->st)));
