@@ -79,7 +79,7 @@ struct Lay {
     static constexpr int OX = 4;                   // left halo columns: boxes start 16-byte aligned
     static constexpr int SW = TX + 2 * OX;         // width of the staged planes
     // the thread that issues the bulk copies: lane 0 of warp 8, a warp with no
-    // ring items (the ring warps are 0-7 and 11), so the serial copy issue
+    // ring items (the ring warps are 0-7, 10 and 15), so the serial copy issue
     // does not lengthen the slowest warp of a band step
     static constexpr int PRODUCER = 256;
     static constexpr int YR = TY + 4, WR = TY + 2, UR = TY + 1, UC = TX + 1;
@@ -115,7 +115,11 @@ struct Lay {
     // dynamic plus the kernel's static shared memory (the candidate counters:
     // 128 bytes, see ptxas -v) within the 227 KB a CTA may use
     static_assert(SMEM + 256 <= 227 * 1024, "shared memory");
-    static_assert(2 * NWR <= 224 && NUR <= 32 + 32, "ring work layout");
+    // the ring work layout (see k1_tile): per set 4 warps of 4 + 4 column and
+    // 17 row items; the u' ring on 2 warps of 8 column items and at most 17
+    // row items
+    static_assert(NWR == 4 * (4 + 4 + 17) && TY == 16 && NUR == 2 * 8 + (TX + 1) && TX + 1 <= 2 * 17,
+                  "ring work layout");
 };
 
 struct K1TArgs {
@@ -151,6 +155,7 @@ struct K1Acc {
 // Per-CTA running state shared by the two tile paths.
 struct K1State {
     K1Acc acc_s, acc_t;
+    float2 ks = make_float2(0.f, 0.f), kc = make_float2(0.f, 0.f);   // packed window sums (s, t)
     K1Acc top_s, top_t;          // |x| above the histogram's range
     unsigned n_y = 0, n_w = 0;   // groups issued so far (thread 0 only)
 };
@@ -175,15 +180,6 @@ __device__ __forceinline__ void append_shared(bool take, float x, float* buf, un
         const bool over = take && k >= (unsigned)Lay::CB;
         append_candidate(over, x, cand, gcnt);
     }
-}
-
-// Counts x into a window accumulator when `take`, without a branch.
-__device__ __forceinline__ void win_add(K1Acc& A, bool take, float x) {
-    Kahan k = A.s;
-    k.add(x);
-    A.n += take ? 1u : 0u;
-    A.s.s = take ? k.s : A.s.s;
-    A.s.c = take ? k.c : A.s.c;
 }
 
 // Counts x into the CTA's histogram (bins of the float key >> kHistShift from
@@ -394,23 +390,35 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
     const bool valid_t = !EDGE || (gi_t < g.n1 && gj_t < g.n2);
     const unsigned o_t = valid_t ? (unsigned)gi_t * (unsigned)g.p2 + (unsigned)gj_t : 0u;
     const int ky_t = (r_t + 2) * SW + (c_t + OX);
-    // Ring w items (both sets, set 0 first) on threads 0..2 NWR-1 (warps 0-6),
-    // ring u' items on warps 7 and 11: each scheduler (warp index mod 4) gets
-    // at most two ring warps besides its four tile warps.
+    // The one-pixel ring: w items on warps 0-7, u' items on warps 10 and 15
+    // (each scheduler, warp index mod 4, gets two or three ring warps besides
+    // its four tile warps).  A column of the ring walks rows 40 floats apart,
+    // so rows r and r + 4 fall in one shared-memory bank: a w warp takes four
+    // consecutive rows of each column, a u' warp eight (the mapping that gave
+    // a warp all 16 rows of a column made K1 0.6 % slower through bank
+    // conflicts).
     int rw_r = 0, rw_c = 0, ru_r = 0, ru_c = 0;
-    const bool has_rw = tid < 2 * L::NWR;
-    const int rw_set = tid >= L::NWR ? 1 : 0;
-    const int ru_k = tid >= 224 && tid < 256 ? tid - 224 : tid >= 352 && tid < 384 ? tid - 352 + 32 : L::NUR;
-    const bool has_ru = ru_k < L::NUR;
+    const int wid = tid >> 5, lane = tid & 31;
+    // w ring: warps 0-7, warp w holds set w / 4 and quarter q = w % 4 of it:
+    // the left and right column items of rows 4q..4q+3 (distinct banks) and
+    // 17 of the 68 row items
+    const bool has_rw = wid < 8 && lane < 25;
+    const int rw_set = wid >= 4 ? 1 : 0;
     if (has_rw) {
-        int k = tid - rw_set * L::NWR;
-        if (k < TX + 2) { rw_r = -1; rw_c = k - 1; }
-        else if ((k -= TX + 2) < TX + 2) { rw_r = TY; rw_c = k - 1; }
-        else if ((k -= TX + 2) < TY) { rw_r = k; rw_c = -1; }
-        else { rw_r = k - TY; rw_c = TX; }
+        const int q = wid & 3;
+        if (lane < 4) { rw_r = 4 * q + lane; rw_c = -1; }
+        else if (lane < 8) { rw_r = 4 * q + lane - 4; rw_c = TX; }
+        else {
+            const int ri = 17 * q + lane - 8;           // 0..67
+            if (ri < TX + 2) { rw_r = -1; rw_c = ri - 1; } else { rw_r = TY; rw_c = ri - (TX + 2) - 1; }
+        }
     }
+    // u' ring: warps 10 and 15, each 8 right-column items and half the row
+    const int uq = wid == 10 ? 0 : wid == 15 ? 1 : -1;
+    const bool has_ru = uq >= 0 && lane < (uq == 0 ? 25 : 24);
     if (has_ru) {
-        if (ru_k < TX + 1) { ru_r = TY; ru_c = ru_k; } else { ru_r = ru_k - (TX + 1); ru_c = TX; }
+        if (lane < 8) { ru_r = 8 * uq + lane; ru_c = TX; }
+        else { ru_r = TY; ru_c = 17 * uq + lane - 8; }
     }
 
     // ---- dual ascent of y1, y2 at this thread's voxel of band tb ----
@@ -482,8 +490,17 @@ __device__ __forceinline__ bool k1_tile(const K1Maps& M, const K1TArgs& a, unsig
         // an inactive window has lo = hi = +inf: nothing is counted or taken
         const float x_s = fabsf(xs), x_t = fabsf(xt);
         const bool hs = valid_t && x_s > W.hi_s, ht = valid_t && x_t > W.hi_t;
-        win_add(S.acc_s, hs, x_s);
-        win_add(S.acc_t, ht, x_t);
+        {
+            // both vectors' compensated sums in packed pairs; a value not
+            // taken adds zero, which leaves the represented sum unchanged
+            const float2 x2 = f2(hs ? x_s : 0.f, ht ? x_t : 0.f);
+            const float2 y2 = sub2(x2, S.kc);
+            const float2 t2 = add2(S.ks, y2);
+            S.kc = sub2(sub2(t2, S.ks), y2);
+            S.ks = t2;
+            S.acc_s.n += hs ? 1u : 0u;
+            S.acc_t.n += ht ? 1u : 0u;
+        }
         const bool cs_ = valid_t && !hs && x_s > W.lo_s, ct_ = valid_t && !ht && x_t > W.lo_t;
         if (__ballot_sync(0xffffffffu, cs_ || ct_)) {     // most warps have no candidate
             append_shared(cs_, x_s, cbuf, ccnt, a.l1.cand[0], &a.sc->acc[0].m);
@@ -677,8 +694,8 @@ __device__ __forceinline__ void k1_run(const K1Maps& maps, const K1TArgs& a, con
         // counts and float-pair sums through the warps, one barrier, thread 0
         // finishes (no FP64 outside thread 0)
         unsigned n4[4] = {S.acc_s.n, S.acc_t.n, S.top_s.n, S.top_t.n};
-        float hi4[4] = {S.acc_s.s.s, S.acc_t.s.s, S.top_s.s.s, S.top_t.s.s};
-        float lo4[4] = {-S.acc_s.s.c, -S.acc_t.s.c, -S.top_s.s.c, -S.top_t.s.c};
+        float hi4[4] = {S.ks.x, S.ks.y, S.top_s.s.s, S.top_t.s.s};
+        float lo4[4] = {-S.kc.x, -S.kc.y, -S.top_s.s.c, -S.top_t.s.c};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
