@@ -4,8 +4,8 @@ A step is one full pass of Algorithm 1 over one cube: the fused stencil pass
 and the finish of its l1 windows, the threshold search (retry window and its
 finish, three radix passes, the gather and its finish) when the fused pass's
 windows missed, and the light pass.  The timed passes run as the solver runs
-them, in CUDA graphs of 16 passes, where a gate kernel skips the seven search
-launches in the passes that need none; K1's duration comes from CUDA events
+them, in CUDA graphs of 16 passes, where the finish of K1's windows skips the
+seven search launches in the passes that need none; K1's duration comes from CUDA events
 captured around it in those graphs.  The workload is the 512 x 512 x 224 synthetic cube
 (sigma 0.1, 5% salt and pepper, stripes on 10% of the columns, dead lines on
 2% of the columns of 10% of the bands), float32 iterates.  The state (about
@@ -321,11 +321,12 @@ GRAPH_PASSES = 16            # passes per CUDA graph (graph_iters), the solver's
 
 def gpu_launches(steps, search_passes, graph_passes=GRAPH_PASSES):
     """Kernels launched in `steps` timed passes: whole graphs of graph_passes
-    passes launch K1, its window finish, the search gate and K2, plus the seven
-    search launches in the passes whose gate opened (search_passes); the
-    remaining passes run eagerly, all ten launches each."""
+    passes launch K1, its window finish (which opens the search launches'
+    conditional node when needed) and K2, plus the seven search launches in
+    the passes whose node opened (search_passes); the remaining passes run
+    eagerly, all ten launches each."""
     in_graphs = (steps // graph_passes) * graph_passes if graph_passes > 0 else 0
-    return 4 * in_graphs + 7 * search_passes + 10 * (steps - in_graphs)
+    return 3 * in_graphs + 7 * search_passes + 10 * (steps - in_graphs)
 
 
 def run_gpu(args):

@@ -160,13 +160,13 @@ IterParams iparams(const gsstv_handle* h, int par) {
 int map_launch(int rc) { return rc == 0 ? GSSTV_OK : rc == -1 ? GSSTV_ERR_ARG : GSSTV_ERR_CUDA; }
 
 // While `st` is being captured into a graph: the launches that body(stream)
-// enqueues become the body of a conditional node, run only when the gate
-// kernel launched just before it finds that one of the n cubes with scalars
-// sc[] needs a threshold search (after K1's window finish, most passes need
-// none, and the seven search launches would each start and return at once).
-// The body is captured from the side stream `side`.
-template <typename F>
-int capture_if_search(cudaStream_t st, cudaStream_t side, Scal* const* sc, int n, F&& body) {
+// enqueues become the body of a conditional node, run only when the launch
+// that decide(cond) enqueues just before it (K1's window finish, or a gate
+// kernel) sets the condition: after K1's window finish most passes need no
+// threshold search, and the seven search launches would each start and
+// return at once.  The body is captured from the side stream `side`.
+template <typename D, typename F>
+int capture_if_search(cudaStream_t st, cudaStream_t side, D&& decide, F&& body) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -175,7 +175,7 @@ int capture_if_search(cudaStream_t st, cudaStream_t side, Scal* const* sc, int n
     if (cs != cudaStreamCaptureStatusActive) return GSSTV_ERR_INTERNAL;
     cudaGraphConditionalHandle cond = 0;
     TRY(cuda_rc(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault)));
-    TRY(map_launch(launch_search_gate(sc, n, cond, st)));
+    TRY(decide(cond));
     TRY(cuda_rc(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd)));
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
@@ -219,10 +219,14 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st, boo
         h->ev_used += 2;
     }
     // the TMA-fed K1 leaves its window's finish to a launch of its own (the
-    // cooperative K1 finishes it in its last CTA)
-    if (h->k1_variant == 1)
-        TRY(map_launch(launch_search_finish(2, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
-                                            k1_tma_grid(h->g, whole, h->k1_chunk), st)));
+    // cooperative K1 finishes it in its last CTA); in a graph that launch, or
+    // a gate kernel, decides whether the search launches run
+    auto k1_finish = [&](int gated, cudaGraphConditionalHandle cond) -> int {
+        if (h->k1_variant == 1)
+            return map_launch(launch_search_finish(2, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
+                                                   k1_tma_grid(h->g, whole, h->k1_chunk), st, gated, cond));
+        return gated ? map_launch(launch_search_gate(&h->sc, 1, cond, st)) : GSSTV_OK;
+    };
     auto search = [&](cudaStream_t s) -> int {
         TRY(map_launch(launch_window(sto, h->g, b, ip, h->sc, h->l1, h->k1_ctas, whole, s)));
         TRY(map_launch(launch_search_finish(0, h->sc, h->l1, 2, h->l1.k1_n, h->l1.k1_s,
@@ -233,10 +237,12 @@ int enqueue_iteration(gsstv_handle* h, int par, bool timed, cudaStream_t st, boo
         TRY(map_launch(launch_search_finish(1, h->sc, h->l1, 2, nullptr, nullptr, 0, s)));
         return GSSTV_OK;
     };
-    if (in_graph)
-        TRY(capture_if_search(st, h->cap2, &h->sc, 1, search));
-    else
+    if (in_graph) {
+        TRY(capture_if_search(st, h->cap2, [&](cudaGraphConditionalHandle c) { return k1_finish(1, c); }, search));
+    } else {
+        TRY(k1_finish(0, 0));
         TRY(search(st));
+    }
     TRY(map_launch(launch_k2(sto, h->g, b, ip, h->sc, h->k2_part, h->k2_cap, whole, st)));
     return GSSTV_OK;
 }
@@ -1003,12 +1009,12 @@ int batch_enqueue(gsstv_batch* b, const std::vector<int>& set, int par, cudaStre
         q.maps = b->dmaps + 2 * c + par;
     }
     TRY(map_launch(launch_k1_batch(cubes, nc, st)));
-    TRY(map_launch(launch_finish_batch(cubes, nc, 2, st)));
-    // the search launches behind a conditional node (the fused solve is
-    // always captured)
-    Scal* scs[kBatchMax];
-    for (int k = 0; k < nc; ++k) scs[k] = cubes[k].sc;
-    TRY(capture_if_search(st, b->cap2, scs, nc, [&](cudaStream_t q) -> int {
+    // K1's window finish, then the search launches behind a conditional node
+    // that it opens (the fused solve is always captured)
+    auto k1_finish = [&](cudaGraphConditionalHandle c) -> int {
+        return map_launch(launch_finish_batch(cubes, nc, 2, st, 1, c));
+    };
+    TRY(capture_if_search(st, b->cap2, k1_finish, [&](cudaStream_t q) -> int {
         TRY(map_launch(launch_window_batch(cubes, nc, q)));
         TRY(map_launch(launch_finish_batch(cubes, nc, 0, q)));
         for (int level = 0; level < 3; ++level) TRY(map_launch(launch_radix_batch(cubes, nc, level, q)));
@@ -1268,7 +1274,10 @@ int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st, bool in_graph = fals
         TRY(map_launch(launch_k1_tma(GSSTV_FP32, x->g, x->maps[par], bufs(x, par), ip, G->sc, G->l1,
                                      G->k1_chunk[s], G->k1p[s], st)));
     }
-    TRY(map_launch(launch_search_finish(2, G->sc, G->l1, 2, G->l1.k1_n, G->l1.k1_s, G->k1p[0].cta_total, st)));
+    auto k1_finish = [&](int gated, cudaGraphConditionalHandle cond) -> int {
+        return map_launch(launch_search_finish(2, G->sc, G->l1, 2, G->l1.k1_n, G->l1.k1_s, G->k1p[0].cta_total, st,
+                                               gated, cond));
+    };
     auto search = [&](cudaStream_t q) -> int {
         for (int s = 0; s < S; ++s) {
             gsstv_handle* x = G->h[s];
@@ -1289,10 +1298,12 @@ int slabs_enqueue(gsstv_slabs* G, int par, cudaStream_t st, bool in_graph = fals
         TRY(map_launch(launch_search_finish(1, G->sc, G->l1, 2, nullptr, nullptr, 0, q)));
         return GSSTV_OK;
     };
-    if (in_graph)
-        TRY(capture_if_search(st, G->cap2, &G->sc, 1, search));
-    else
+    if (in_graph) {
+        TRY(capture_if_search(st, G->cap2, [&](cudaGraphConditionalHandle c) { return k1_finish(1, c); }, search));
+    } else {
+        TRY(k1_finish(0, 0));
         TRY(search(st));
+    }
     for (int s = 0; s < S; ++s) {
         gsstv_handle* x = G->h[s];
         TRY(map_launch(launch_k2(GSSTV_FP32, x->g, bufs(x, par), ip, G->sc, G->k2_part, G->k2_cap, G->k2p[s], st)));

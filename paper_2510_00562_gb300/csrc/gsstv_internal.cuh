@@ -162,12 +162,15 @@ struct Scal {
     // that follows it: its window statistics and candidates, its histogram
     int k1_win[2], k1_hist[2];
     long long gate_opens;      // passes whose threshold search launches ran (graphs)
+    unsigned int fin_ticket;   // CTAs of K1's window finish done (the last sets the search gate)
+    unsigned int pad2;
 };
 
 constexpr int kHistBins = 2048;        // radix histogram bins per vector
 constexpr unsigned kCandCap = 1u << 20; // candidate capacity per vector
 constexpr int kNarrowBins = 2048;        // bins of one narrowing round of a candidate list
-constexpr double kCandTarget = 393216.0;  // K1's window is sized for at most about this many candidates
+constexpr double kCandTarget = 65536.0;   // K1's window is sized for at most about this many candidates,
+constexpr double kCandTargetWide = 393216.0;  // or this many while the thresholds move fast (histogram on)
 constexpr double kRetryTarget = 262144.0; // a retry window after a miss: at most about this many
 constexpr unsigned kGatherMax = 1u << 16; // a radix bracket this small is gathered, a larger one refined
 // K1's histogram of |x| near the predicted threshold: 1024 bins of 1/256
@@ -435,14 +438,19 @@ int launch_window(int storage, const Geom& g, const IterBufs& b, const IterParam
                   const L1Work& w, int part_cap, const SlabPart& sp, cudaStream_t st);
 int launch_k2(int storage, const Geom& g, const IterBufs& b, const IterParams& p, Scal* sc,
               double* part, int part_cap, const SlabPart& sp, cudaStream_t st);
-// The finish of the retry window (mode 0; parts: CTAs of the window pass(es),
+// Sets `cond` (a graph conditional handle) to whether any of the n cubes
+// whose scalars are sc[] needs a threshold search after K1's finish (for the
+// cooperative K1, whose last CTA finishes its windows itself).
+int launch_search_gate(Scal* const* sc, int n, cudaGraphConditionalHandle cond, cudaStream_t st);
+// The finish of K1's windows (mode 2; parts: K1's CTAs, four partials each in
+// pn / ps), of the retry window (mode 0; parts: CTAs of the window pass(es),
 // their partial sums in pn / ps) or of the gathered radix bracket (mode 1),
 // for every vector that needs it: one launch after the pass(es) it finishes.
-// Sets `cond` (a graph conditional handle) to whether any of the n cubes
-// whose scalars are sc[] needs a threshold search after K1's finish.
-int launch_search_gate(Scal* const* sc, int n, cudaGraphConditionalHandle cond, cudaStream_t st);
+// gated (mode 2 in a graph): its last CTA also sets `cond` to whether a
+// threshold search is still needed.
 int launch_search_finish(int mode, Scal* sc, const L1Work& w, int nvec, const unsigned long long* pn,
-                         const double* ps, int parts, cudaStream_t st);
+                         const double* ps, int parts, cudaStream_t st, int gated = 0,
+                         cudaGraphConditionalHandle cond = 0);
 int k2_grid_ctas(const Geom& g);
 
 // ---------------------------------------------------------------------------
@@ -471,7 +479,8 @@ int launch_k1_batch(const BatchCube* cubes, int n, cudaStream_t st);
 int launch_window_batch(const BatchCube* cubes, int n, cudaStream_t st);
 int launch_radix_batch(const BatchCube* cubes, int n, int level, cudaStream_t st);
 int launch_gather_batch(const BatchCube* cubes, int n, cudaStream_t st);
-int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st);
+int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st, int gated = 0,
+                        cudaGraphConditionalHandle cond = 0);
 int launch_k2_batch(const BatchCube* cubes, int n, cudaStream_t st);
 int batch_configure();
 

@@ -698,7 +698,10 @@ static __device__ void l1_record_tau(L1Ctl& c, double tau_new, double m_used, do
     } else {
         hw = 2.0 * fabs(d1) + 1e-7 * tau_new;
     }
-    if (c.dens > 0.0) hw = fmin(hw, 0.5 * kCandTarget / c.dens);
+    // a wide window while the thresholds move fast (the passes after a miss,
+    // with K1's histogram on), where a hit saves a retry pass; else a narrow
+    // one, which K1 and the finish handle faster
+    if (c.dens > 0.0) hw = fmin(hw, 0.5 * (c.hist_left > 0 ? kCandTargetWide : kCandTarget) / c.dens);
     // the histogram of the next pass: four octaves from a quarter of the
     // predicted threshold
     c.hbase = center > 0.0 ? (__float_as_uint(__double2float_rd(0.25 * center)) >> kHistShift) : 0u;

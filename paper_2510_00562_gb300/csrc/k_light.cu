@@ -680,10 +680,39 @@ __device__ __forceinline__ void finish_body(const SearchArgs& a, int mode, const
 }
 
 // one CTA per vector
+// After K1's window finish (mode 2) in a graph: the last of the launch's
+// CTAs opens the conditional node of the search launches when a cube still
+// needs a search (one thread, so that no two calls race).  need_any() reads the
+// cubes' flags after every CTA's have landed.
+template <typename F>
+__device__ __forceinline__ void finish_gate(Scal* counter, unsigned total, cudaGraphConditionalHandle cond,
+                                            F&& need_any) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&counter->fin_ticket, 1u) == total - 1u;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        counter->fin_ticket = 0u;
+        const unsigned need = need_any() ? 1u : 0u;
+        if (need) counter->gate_opens++;
+        cudaGraphSetConditional(cond, need);
+    }
+}
+__device__ __forceinline__ bool scal_needs_search(const Scal* s) {
+    return !__ldcg(&s->done) && (__ldcg(&s->ctl[0].need) != NEED_NONE || __ldcg(&s->ctl[1].need) != NEED_NONE);
+}
+
+// one CTA per vector; gated: a graph's conditional node waits on this launch
 __global__ void __launch_bounds__(kFinishThreads) k_search_finish(const SearchArgs a, int mode,
                                                                    const unsigned long long* pn,
-                                                                   const double* ps, int parts) {
+                                                                   const double* ps, int parts, int gated,
+                                                                   cudaGraphConditionalHandle cond) {
     finish_body(a, mode, pn, ps, parts, blockIdx.x);
+    if (gated) finish_gate(a.sc, gridDim.x, cond, [&] { return scal_needs_search(a.sc); });
 }
 
 // out = soft(x, tau) for the standalone projection
@@ -934,10 +963,17 @@ __global__ void __launch_bounds__(NT) k_gather_batch(const __grid_constant__ Sea
 }
 // one CTA per cube and vector
 __global__ void __launch_bounds__(kFinishThreads) k_finish_batch(const __grid_constant__ SearchBatchTab t,
-                                                                  const int mode) {
+                                                                  const int mode, int gated,
+                                                                  cudaGraphConditionalHandle cond) {
     const SearchCube& q = t.c[blockIdx.x >> 1];
-    if (__ldcg(&q.a.sc->done)) return;
-    finish_body(q.a, mode, q.pn, q.ps, q.parts, blockIdx.x & 1);
+    if (!__ldcg(&q.a.sc->done)) finish_body(q.a, mode, q.pn, q.ps, q.parts, blockIdx.x & 1);
+    // every CTA counts, a stopped cube's too (the first cube's scalars hold the count)
+    if (gated)
+        finish_gate(t.c[0].a.sc, gridDim.x, cond, [&] {
+            bool any = false;
+            for (int c = 0; c < t.n; ++c) any = any || scal_needs_search(t.c[c].a.sc);
+            return any;
+        });
 }
 __global__ void __launch_bounds__(NT, 3) k2_batch(const __grid_constant__ K2BatchTab t) {
     const int c = batch_cube_of(t.start, t.n, blockIdx.x);
@@ -1009,9 +1045,10 @@ int light_configure(int storage) {
 }
 
 int launch_search_finish(int mode, Scal* sc, const L1Work& w, int nvec, const unsigned long long* pn,
-                         const double* ps, int parts, cudaStream_t st) {
+                         const double* ps, int parts, cudaStream_t st, int gated,
+                         cudaGraphConditionalHandle cond) {
     SearchArgs a{sc, w, nvec};
-    k_search_finish<<<nvec, kFinishThreads, kFinishSmem, st>>>(a, mode, pn, ps, parts);
+    k_search_finish<<<nvec, kFinishThreads, kFinishSmem, st>>>(a, mode, pn, ps, parts, gated, cond);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -1125,12 +1162,13 @@ int launch_search_gate(Scal* const* sc, int n, cudaGraphConditionalHandle cond, 
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st) {
+int launch_finish_batch(const BatchCube* cubes, int n, int mode, cudaStream_t st, int gated,
+                        cudaGraphConditionalHandle cond) {
     SearchBatchTab t{};
     if (search_table(cubes, n, t, [](const BatchCube&, const SlabPart&) { return 1; }) < 0) return -1;
     if (mode == 2)                       // K1's partials: one set per CTA of the cube's K1 grid
         for (int c = 0; c < n; ++c) t.c[c].parts = k1_tma_grid(cubes[c].g, whole_cube(cubes[c].g), cubes[c].k1_chunk);
-    k_finish_batch<<<2 * n, kFinishThreads, kFinishSmem, st>>>(t, mode);
+    k_finish_batch<<<2 * n, kFinishThreads, kFinishSmem, st>>>(t, mode, gated, cond);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -1283,7 +1321,7 @@ int l1_project_standalone(const float* x, long long n, double radius, float* out
         for (int level = 0; level < 3 && rc == 0; ++level) rc = launch_radix_src(src, n, a, level, st);
         if (rc == 0) {
             k_gather<FlatSrc><<<gather_grid_n(n), NT, 0, st>>>(src, a);
-            k_search_finish<<<1, kFinishThreads, kFinishSmem, st>>>(a, 1, nullptr, nullptr, 0);
+            k_search_finish<<<1, kFinishThreads, kFinishSmem, st>>>(a, 1, nullptr, nullptr, 0, 0, 0);
             k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
             if (cudaGetLastError() != cudaSuccess) rc = -3;
         }
@@ -1382,7 +1420,7 @@ int l1_project_noalloc(const float* x, long long n, double radius, float* out, d
     for (int level = 0; level < 3; ++level)
         if (launch_radix_src(src, n, a, level, st) != 0) return -3;
     k_gather<FlatSrc><<<gather_grid_n(n), NT, 0, st>>>(src, a);
-    k_search_finish<<<1, kFinishThreads, kFinishSmem, st>>>(a, 1, nullptr, nullptr, 0);
+    k_search_finish<<<1, kFinishThreads, kFinishSmem, st>>>(a, 1, nullptr, nullptr, 0, 0, 0);
     k_apply_flat<<<grid_for(n), NT, 0, st>>>(x, out, n, sc);
     if (cudaGetLastError() != cudaSuccess) return -3;
     double t = 0.0;
