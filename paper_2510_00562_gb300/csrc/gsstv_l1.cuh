@@ -387,12 +387,16 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
     }
     const bool staged = stage && m <= stage_cap;
     const bool pre_staged = cand == nullptr;           // the narrowed values already sit in the stage
-    if (pre_staged && m <= kWarpMichelot) {
-        // A few values (one narrow bin): warp 0 alone runs Michelot's steps
-        // on them, with shuffles instead of CTA barriers; the FP64 steps on
-        // lane 0.
+    if ((pre_staged || staged) && m <= kWarpMichelot) {
+        // A few values (one narrow bin, or a small window): warp 0 alone runs
+        // Michelot's steps on them, with shuffles instead of CTA barriers;
+        // the FP64 steps on lane 0.
         __shared__ double ww_tau;
         __shared__ int ww_rc;
+        if (!pre_staged) {
+            for (unsigned k = threadIdx.x; k < m; k += blockDim.x) stage[k] = __ldcg(cand + k);
+            __syncthreads();
+        }
         if (threadIdx.x < 32) {
             const unsigned lane = threadIdx.x;
             Kahan ks;
@@ -406,6 +410,7 @@ static __device__ int l1_window_finish(double n_hi, double s_hi, const float* ca
                 const double sum_c = (double)h + (double)l;
                 const double n_all = n_hi + (double)m;
                 const double phi_lo = s_hi + sum_c - n_all * theta_lo - r;
+                if (info) { info->phi_lo = phi_lo; info->n_lo = n_all; }   // (thread 0's)
                 if (phi_lo < 0.0) {
                     state = theta_lo <= 0.0 ? 2 : 3;
                 } else {
