@@ -188,8 +188,8 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
         // Exact sums in units of u0, the ulp at the window's lowest key: every
         // float in the window is an integer multiple of u0 (below 2^40 of
         // them while the window spans at most 16 binary orders), so a bin's
-        // count and sum and their suffix sums are exact 64-bit integers; FP64
-        // appears only in the comparisons of phi with 0 at a few bin edges.
+        // count and sum and their suffix sums are exact 64-bit integers, and
+        // the sign of phi at a bin edge follows from an integer comparison.
         const unsigned k0 = klo + 1u;
         const int e0 = max((int)((k0 >> 23) & 0xffu), 1);
         const double u0 = key_ulp(k0);
@@ -222,6 +222,29 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
         // which the lanes then find two bins each.
         if (threadIdx.x < 32) {
             const int lane = (int)threadIdx.x;
+            // phi at an edge e inside the window (b > 0) is A + u0 X with
+            // A = s_hi - r and the exact integer X = Ssuf - (Nsuf + n_hi) e/u0,
+            // so phi >= 0 exactly when X >= T = ceil(-A / u0) (u0 a power of
+            // two: the quotient is exact): the lanes test in integers, lane 0
+            // alone computes T in FP64.  Windows so narrow against the sums
+            // that T leaves 62 bits take the FP64 test.
+            long long T = 0, NH = 0;
+            int int_ok = 0;
+            if (lane == 0) {
+                const double q = ceil(-(s_hi - r) / u0);
+                int_ok = fabs(q) < 4.6e18 && n_hi >= 0.0 && n_hi < 9.0e15;
+                T = int_ok ? (long long)q : 0;
+                NH = int_ok ? (long long)n_hi : 0;
+            }
+            int_ok = __shfl_sync(0xffffffffu, int_ok, 0);
+            T = __shfl_sync(0xffffffffu, T, 0);
+            NH = __shfl_sync(0xffffffffu, NH, 0);
+            auto edge_ok = [&](int b, unsigned long long Nsuf, unsigned long long Ssuf) -> bool {
+                if (b == 0 || !int_ok) return edge_phi(b, Nsuf, Ssuf) >= 0.0;
+                const unsigned lk = (base + (unsigned)b) << shift;
+                const __int128 X = (__int128)Ssuf - (__int128)(Nsuf + (unsigned long long)NH) * (__int128)V(lk);
+                return X >= (__int128)T;
+            };
             const int per = (nb + 31) / 32;
             const int c0 = lane * per, c1 = min(nb, c0 + per);
             unsigned long long Nc = 0, Sc = 0;
@@ -234,7 +257,7 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
                 const unsigned long long y = __shfl_down_sync(0xffffffffu, Si, o);
                 if (lane + o < 32) { Ni += x; Si += y; }
             }
-            const bool ok = c0 < c1 && edge_phi(c0, Ni, Si) >= 0.0;
+            const bool ok = c0 < c1 && edge_ok(c0, Ni, Si);
             const unsigned okm = __ballot_sync(0xffffffffu, ok);
             if (okm == 0u) {
                 if (lane == 0) {
@@ -259,8 +282,8 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
                     const unsigned long long y = __shfl_down_sync(0xffffffffu, Sj, o);
                     if (lane + o < 32) { Nj += x; Sj += y; }
                 }
-                const bool okA = bA < l1 && edge_phi(bA, Nup + Nj, Sup + Sj) >= 0.0;
-                const bool okB = bB < l1 && edge_phi(bB, Nup + Nj - nA, Sup + Sj - sA) >= 0.0;
+                const bool okA = bA < l1 && edge_ok(bA, Nup + Nj, Sup + Sj);
+                const bool okB = bB < l1 && edge_ok(bB, Nup + Nj - nA, Sup + Sj - sA);
                 const int mine = okB ? bB : okA ? bA : -1;
                 const int best = __reduce_max_sync(0xffffffffu, mine);
                 if (mine == best) {
