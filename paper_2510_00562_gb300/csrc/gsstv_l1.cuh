@@ -693,12 +693,15 @@ static __device__ int l1_hist_bracket(const unsigned* hist_g, unsigned hbase, do
 }
 
 // Records tau of this iteration and places the window of the next one around
-// the linear extrapolation of the last two thresholds.  After a window hit the
-// half-width covers twice the last change of the step plus a tenth of the step
-// (the extrapolation error of a smoothly converging sequence); after a miss,
-// twice the step itself.  Either is capped so that about kCandTarget
-// candidates are expected (density measured at the last window).  `hit`: tau
-// came from K1's window.  Thread 0 only.
+// the extrapolation of the last thresholds.  In the passes after a miss
+// (K1's histogram on) the window spans the linear and the quadratic
+// extrapolations; otherwise it is centred on the linear one, and after a window
+// hit the half-width covers twice the last change of the step plus a tenth of
+// the step (the extrapolation error of a smoothly converging sequence), after
+// a miss twice the step itself.  Each is capped so that about kCandTarget
+// (kCandTargetWide while the histogram is on) candidates are expected (density
+// measured at the last window).  `hit`: tau came from K1's window.  Thread 0
+// only.
 static __device__ void l1_record_tau(L1Ctl& c, double tau_new, double m_used, double width_used, bool hit) {
     c.tau_prev2 = c.tau_prev;
     c.have_prev2 = c.have_prev;
@@ -716,10 +719,18 @@ static __device__ void l1_record_tau(L1Ctl& c, double tau_new, double m_used, do
     }
     const bool trend = c.have_prev && c.tau_prev > 0.0;
     const double d1 = trend ? tau_new - c.tau_prev : 0.0;
-    const double center = tau_new + d1;
+    double center = tau_new + d1;
     double hw;
     if (!trend) {
         hw = 1e-3 * tau_new;
+    } else if (c.hist_left > 0 && c.have_prev2 && c.tau_prev2 > 0.0) {
+        // the passes after a miss, while the thresholds move fast: the window
+        // spans the linear and the quadratic extrapolations (tau + d1 and
+        // tau + 2 d1 - d0) with a margin of half their distance and a tenth
+        // of the step, after a retry or an exact search as after a hit
+        const double d0 = c.tau_prev - c.tau_prev2;
+        center = tau_new + d1 + 0.5 * (d1 - d0);
+        hw = fabs(d1 - d0) + 0.1 * fabs(d1) + 1e-7 * tau_new;
     } else if (hit && c.have_prev2 && c.tau_prev2 > 0.0) {
         const double d0 = c.tau_prev - c.tau_prev2;
         hw = 2.0 * fabs(d1 - d0) + 0.1 * fabs(d1) + 1e-7 * tau_new;
