@@ -78,20 +78,40 @@ def k1_variant():
     return "coop" if os.environ.get("GSSTV_K1") == "coop" else "tma"
 
 
+def k1_source_sha(variant):
+    """sha256 of K1's translation unit: its source and, depth first in include
+    order, every header of the package it includes (each counted once)."""
+    import hashlib
+    import re
+    from paper_2510_00562_gb300 import build
+    seen, parts = set(), []
+
+    def add(name):
+        if name in seen:
+            return
+        seen.add(name)
+        data = open(os.path.join(build.CSRC, name), "rb").read()
+        parts.append(data)
+        for inc in re.findall(rb'^\s*#\s*include\s+"([^"]+)"', data, re.M):
+            if os.path.exists(os.path.join(build.CSRC, inc.decode())):
+                add(inc.decode())
+
+    add(K1_SOURCE[variant])
+    return hashlib.sha256(b"".join(parts)).hexdigest()
+
+
 def k1_traffic_record(storage, variant):
-    """ncu dram bytes per voxel of one K1 launch, if recorded for the current source."""
+    """ncu dram bytes per voxel of one K1 launch, if recorded for the current
+    translation unit of that kernel (source and included headers)."""
     path = os.path.join(ROOT, "profiles", "k1_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return None
-    import hashlib
-    from paper_2510_00562_gb300 import build
     ent = rec.get(variant)
     if not ent:
         return None
-    src = open(os.path.join(build.CSRC, K1_SOURCE[variant]), "rb").read()
-    if ent.get("sha256") != hashlib.sha256(src).hexdigest():
+    if ent.get("sha256") != k1_source_sha(variant):
         return None
     st = ent.get(storage)
     return float(st["bytes_per_voxel"]) if st else None
@@ -372,11 +392,9 @@ def run_gpu(args):
     ms_max = max_over_ranks(ms, dist)
     value = job_throughput(world, nvox, args.steps, ms_max)
 
-    pf = None
-    if not args.no_precision_form and args.storage == "fp32" and world == 1:
-        pf = precision_form(sol, pb, args.shape, args.pf_iters, args.steps)
-
-    # end to end through the public host API: copies in, solve, copies out
+    # end to end through the public host API: copies in, solve, copies out;
+    # right after the device-timed region, so that both see the GPU in the
+    # same state (not after the precision form's thousand passes)
     sol.set_params(make_params(eps=pb["eps"], alpha=pb["alpha"], beta=pb["beta"], omega=0.03,
                                max_iter=args.steps, storage=args.storage, graph_iters=16))
     vh = torch.from_numpy(pb["v"]).pin_memory()
@@ -386,11 +404,16 @@ def run_gpu(args):
     sol.solve_host(vh, uh, sh, th)           # untimed: the solver's graphs built for these parameters
     torch.cuda.synchronize()
     barrier(dist)
-    t0 = time.perf_counter()
-    sol.solve_host(vh, uh, sh, th)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    with ClockSampler(local) as clk_e2e:
+        t0 = time.perf_counter()
+        sol.solve_host(vh, uh, sh, th)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     e2e_value = world * nvox * args.steps / e2e_s
+
+    pf = None
+    if not args.no_precision_form and args.storage == "fp32" and world == 1:
+        pf = precision_form(sol, pb, args.shape, args.pf_iters, args.steps)
     sol.close()
     quality = None
     if rank == 0:
@@ -437,7 +460,8 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * nvox / args.steps,
                 "d2h_bytes_per_step": 3 * 4 * nvox / args.steps,
                 "note": "one gsstv_solve_host call of `steps` iterations after an untimed one (the "
-                        "solver's graphs built): pinned H2D of v, state reset, iterations, D2H of u, s, t"},
+                        "solver's graphs built): pinned H2D of v, state reset, iterations, D2H of u, s, t",
+                "clocks": clk_e2e.summary()},
         "gpu_launches": gpu_launches(args.steps, st["search_passes"], args.graph_passes),
         "quality": quality,
     }

@@ -97,17 +97,21 @@ __device__ __forceinline__ NarrowGeom narrow_geom(unsigned klo, unsigned khi) {
     g.ok = max((int)((khi >> 23) & 0xffu), 1) - max((int)(((klo + 1u) >> 23) & 0xffu), 1) <= 16;
     return g;
 }
-// Counts a key of the window into a narrowing histogram h: kNarrowBins bin
-// counts, then the sums of the low and of the high 10 bits of the keys'
-// residues below the bin edge (shared or global memory).
+// A narrowing histogram is kNarrowBins 64-bit words (8-byte aligned, shared
+// or global memory), bin b holding its count in the bits from kNarrowCntBit
+// up and the sum of its keys' residues below the bin edge in the bits below:
+// a residue is below 2^20 (shift <= 20), and a histogram that is read holds at
+// most kCandCap = 2^20 keys, so the sum stays below 2^40 and the count below
+// 2^22.  One 64-bit atomic counts a key.
+constexpr int kNarrowCntBit = 42;
 __device__ __forceinline__ void narrow_add(unsigned* h, const NarrowGeom& g, unsigned key) {
     const int b = (int)((key >> g.shift) - g.base);
     const unsigned res = key - ((key >> g.shift) << g.shift);
-    atomicAdd(h + b, 1u);
-    if (res) {
-        atomicAdd(h + kNarrowBins + b, res & 1023u);
-        atomicAdd(h + 2 * kNarrowBins + b, res >> 10);
-    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(h) + b, (1ull << kNarrowCntBit) + res);
+}
+__device__ __forceinline__ unsigned narrow_count(unsigned long long w) { return (unsigned)(w >> kNarrowCntBit); }
+__device__ __forceinline__ unsigned long long narrow_res(unsigned long long w) {
+    return w & ((1ull << kNarrowCntBit) - 1ull);
 }
 // The key histogram of vector v's candidate list when every one of its m
 // candidates was counted into it (built by the passes that appended them,
@@ -121,7 +125,7 @@ __device__ __forceinline__ void narrow_clear(const L1Work& w, int v) {
     const unsigned used = __ldcg(w.nbinned + v);
     __syncthreads();
     if (used == 0u) return;
-    for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) w.nh[v * 3 * kNarrowBins + k] = 0u;
+    for (int k = threadIdx.x; k < 2 * kNarrowBins; k += blockDim.x) w.nh[v * 3 * kNarrowBins + k] = 0u;
     if (threadIdx.x == 0) w.nbinned[v] = 0u;
 }
 
@@ -147,9 +151,7 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
             for_each_candidate(cand, m, f);
         }
     };
-    unsigned* cnt = scr;
-    unsigned* rlo = scr + kNarrowBins;
-    unsigned* rhi = scr + 2 * kNarrowBins;
+    const unsigned long long* hw = reinterpret_cast<const unsigned long long*>(scr);
     for (int round = 0; round < 8; ++round) {
         const NarrowGeom ng = narrow_geom(klo, khi);
         const int shift = ng.shift;
@@ -163,7 +165,7 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
             // CTA copying from L2 is bound by the loads' latency)
             const uint4* p4 = reinterpret_cast<const uint4*>(pre);
             uint4* s4 = reinterpret_cast<uint4*>(scr);
-            constexpr int kW4 = 3 * kNarrowBins / 4;
+            constexpr int kW4 = 2 * kNarrowBins / 4;
             uint4 q[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -177,7 +179,7 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
             }
             for (int k = (int)threadIdx.x + 2 * (int)blockDim.x; k < kW4; k += blockDim.x) s4[k] = __ldcg(p4 + k);
         } else {
-            for (int k = threadIdx.x; k < 3 * kNarrowBins; k += blockDim.x) scr[k] = 0u;
+            for (int k = threadIdx.x; k < 2 * kNarrowBins; k += blockDim.x) scr[k] = 0u;
             __syncthreads();
             each([&](float x, unsigned) {
                 const unsigned key = __float_as_uint(x);
@@ -200,8 +202,8 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
         };
         auto bin_int = [&](int b) -> unsigned long long {        // sum of bin b, in units of u0
             const unsigned lk = (base + (unsigned)b) << shift;
-            const unsigned long long res = (unsigned long long)rhi[b] * 1024ull + rlo[b];
-            return (unsigned long long)cnt[b] * V(lk) + (res << (max((int)((lk >> 23) & 0xffu), 1) - e0));
+            const unsigned long long w = hw[b];
+            return (unsigned long long)narrow_count(w) * V(lk) + (narrow_res(w) << (max((int)((lk >> 23) & 0xffu), 1) - e0));
         };
         // phi at an edge with the bins from b up and everything above the window
         auto phi_at = [&](double e, unsigned long long e_int, unsigned long long Nsuf, unsigned long long Ssuf) {
@@ -248,7 +250,7 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
             const int per = (nb + 31) / 32;
             const int c0 = lane * per, c1 = min(nb, c0 + per);
             unsigned long long Nc = 0, Sc = 0;
-            for (int b = c0; b < c1; ++b) { Nc += cnt[b]; Sc += bin_int(b); }
+            for (int b = c0; b < c1; ++b) { Nc += narrow_count(hw[b]); Sc += bin_int(b); }
             // inclusive suffix over the lanes: the bins from c0 up
             unsigned long long Ni = Nc, Si = Sc;
 #pragma unroll
@@ -273,8 +275,8 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
                 const unsigned long long Nup = __shfl_sync(0xffffffffu, Ni - Nc, L);
                 const unsigned long long Sup = __shfl_sync(0xffffffffu, Si - Sc, L);
                 const int bA = l0 + 2 * lane, bB = bA + 1;
-                const unsigned long long nA = bA < l1 ? cnt[bA] : 0ull, sA = bA < l1 ? bin_int(bA) : 0ull;
-                const unsigned long long nB = bB < l1 ? cnt[bB] : 0ull, sB = bB < l1 ? bin_int(bB) : 0ull;
+                const unsigned long long nA = bA < l1 ? narrow_count(hw[bA]) : 0ull, sA = bA < l1 ? bin_int(bA) : 0ull;
+                const unsigned long long nB = bB < l1 ? narrow_count(hw[bB]) : 0ull, sB = bB < l1 ? bin_int(bB) : 0ull;
                 unsigned long long Nj = nA + nB, Sj = sA + sB;      // inclusive suffix from bA
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -299,7 +301,7 @@ static __device__ int l1_narrow(const float* cand, bool cand_shared, unsigned m,
         __syncthreads();
         const int kb = sh_i[0];
         if (kb < 0) { __syncthreads(); return 1; }
-        const unsigned count = cnt[kb];
+        const unsigned count = narrow_count(hw[kb]);
         n_hi = sh_d[0];
         s_hi = sh_d[1];
         const unsigned nlo = kb == 0 ? klo : ((base + (unsigned)kb) << shift) - 1u;
