@@ -246,9 +246,12 @@ struct CubeSrc {
     int o0, nb;         // the stored bands [o0, o0 + nb) this launch visits
     // Calls f(valid, |s~|, |t~|) for every voxel this thread owns, four
     // columns at a time in row order; every lane of a warp makes the same
-    // number of calls (warp-collective work inside f is allowed).
+    // number of calls (warp-collective work inside f is allowed).  want_s /
+    // want_t: whether the pass needs |s~| / |t~| (uniform over the launch); the
+    // inputs of a vector not wanted are not read, and its value passed to f is
+    // meaningless.
     template <typename F>
-    __device__ void visit(const int bid, const int nblk, F&& f) const {
+    __device__ void visit(const int bid, const int nblk, F&& f, const bool want_s, const bool want_t) const {
         const float cs = (float)(1.0 - sc->c[parity]);
         const unsigned quads = (unsigned)g.p2 / 4u;
         const unsigned n1 = (unsigned)g.n1;
@@ -263,11 +266,13 @@ struct CubeSrc {
             float4 s4 = make_float4(0, 0, 0, 0), t4 = s4, y34 = s4, yu4 = s4, q4 = s4;
             if (live) {
                 const long long o = (long long)row * g.p2 + j;
-                s4 = Vec4<T>::ld(s + o);
-                t4 = Vec4<T>::ld(t + o);
-                y34 = Vec4<T>::ld(y3 + o);
+                if (want_s) s4 = Vec4<T>::ld(s + o);
+                if (want_t) {
+                    t4 = Vec4<T>::ld(t + o);
+                    y34 = Vec4<T>::ld(y3 + o);
+                    if (i >= 1) yu4 = Vec4<T>::ld(y3 + o - g.p2);
+                }
                 q4 = Vec4<T>::ld(q + o);
-                if (i >= 1) yu4 = Vec4<T>::ld(y3 + o - g.p2);
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -286,7 +291,7 @@ struct FlatSrc {
     const float* x;
     long long n;
     template <typename F>
-    __device__ void visit(const int bid, const int nblk, F&& f) const {
+    __device__ void visit(const int bid, const int nblk, F&& f, bool, bool) const {
         for (long long base = bid * (long long)blockDim.x; base < n; base += (long long)nblk * blockDim.x) {
             const long long l = base + threadIdx.x;
             const bool valid = l < n;
@@ -350,7 +355,7 @@ __device__ __forceinline__ void radix_body(const Src& src, const SearchArgs& a, 
             const unsigned key = __float_as_uint(x1);
             insert(1, valid && lv.inside(key, pre1), key);
         }
-    });
+    }, need[0], need[1]);
     __syncthreads();
     for (int k = threadIdx.x; k < 2 * kHistBins; k += NT) {
         if ((k % kHistBins) >= nb) continue;
@@ -466,7 +471,7 @@ __device__ __forceinline__ void gather_body(const Src& src, const SearchArgs& a,
     src.visit(bid, nblk, [&](bool valid, float x0, float x1) {
         if (need[0]) bc.append(0, valid && x0 > lo0 && x0 <= hi0, x0, a.w.cand[0], &a.sc->acc[0].m);
         if (need[1]) bc.append(1, valid && x1 > lo1 && x1 <= hi1, x1, a.w.cand[1], &a.sc->acc[1].m);
-    });
+    }, need[0], need[1]);
     bc.flush(a.w.cand, a.sc);
     bc.bin(0);
     bc.bin(1);
@@ -507,7 +512,7 @@ __device__ __forceinline__ void window_body(const Src& src, const SearchArgs& a,
             if (hi) { w1.n++; w1.s.add(x1); }
             bc.append(1, valid && !hi && x1 > lo1, x1, a.w.cand[1], &a.sc->acc[1].m);
         }
-    });
+    }, need[0], need[1]);
     bc.flush(a.w.cand, a.sc);
     bc.bin(0);
     bc.bin(1);
