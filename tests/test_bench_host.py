@@ -70,3 +70,26 @@ def test_reference_crop_is_bounded():
 def test_oracle_timing_runs_on_a_small_crop():
     value, dt = bench.time_oracle(1, 0, shape=(16, 16, 8))
     assert value > 0 and dt > 0
+
+
+def test_k1_traffic_record_is_keyed_on_the_translation_unit(tmp_path, monkeypatch):
+    """The recorded DRAM bytes of K1 are valid for one translation unit: its
+    source and the package headers it includes.  A change to an included
+    header (as a change to the source) invalidates the record, so the bench
+    line reports no traffic for a kernel the counters were not taken on."""
+    import shutil
+    from paper_2510_00562_gb300 import build
+    csrc = tmp_path / "csrc"
+    shutil.copytree(build.CSRC, csrc, ignore=shutil.ignore_patterns("*.o", "*.so"))
+    monkeypatch.setattr(build, "CSRC", str(csrc))
+    sha0 = bench.k1_source_sha("tma")
+    assert sha0 == bench.k1_source_sha("tma")
+    # the committed record matches the tree as it stands
+    rec = json.load(open(os.path.join(ROOT, "profiles", "k1_traffic.json")))
+    assert rec["tma"]["sha256"] == sha0
+    assert bench.k1_traffic_record("fp32", "tma") == rec["tma"]["fp32"]["bytes_per_voxel"]
+    # a header two includes deep (k_stencil_tma.cu -> gsstv_l1.cuh -> gsstv_internal.cuh)
+    hdr = csrc / "gsstv_internal.cuh"
+    hdr.write_bytes(hdr.read_bytes() + b"\n// edited\n")
+    assert bench.k1_source_sha("tma") != sha0
+    assert bench.k1_traffic_record("fp32", "tma") is None
