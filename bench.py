@@ -297,10 +297,30 @@ def time_oracle_all_cores(steps, warmup, shape=CPU_SAMPLE, procs=None):
     return procs * nvox * steps / dt, dt, procs
 
 
-def reference_crop(steps, warmup, budget_s=120.0, rate=1.5e6):
+ORACLE_BYTES_PER_VOXEL = 800     # peak resident memory of one oracle process (measured: about 690)
+
+
+def mem_available():
+    """Bytes of memory available to new processes (Linux MemAvailable), or None."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def reference_crop(steps, warmup, budget_s=120.0, rate=1.5e6, procs=1, avail=None):
     """Spatial crop of the workload sized so that steps + warmup oracle passes
-    take about budget_s seconds at ~rate voxel-iterations per second."""
+    take about budget_s seconds at ~rate voxel-iterations per second, and so
+    that `procs` oracle processes together hold at most 60 % of the available
+    memory."""
     per_step = budget_s * rate / max(steps + warmup, 1)
+    avail = mem_available() if avail is None else avail
+    if avail:
+        per_step = min(per_step, 0.6 * avail / (max(procs, 1) * ORACLE_BYTES_PER_VOXEL))
     side = int(math.sqrt(per_step / SHAPE[2]) // 16 * 16)
     side = max(16, min(side, 512))
     return (side, side, SHAPE[2])
@@ -311,8 +331,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     # one crop per host core, each the size one core runs in the time budget
-    crop = reference_crop(args.steps, args.warmup)
-    value, dt, cores = time_oracle_all_cores(args.steps, args.warmup, shape=crop)
+    cores = host_cores()
+    crop = reference_crop(args.steps, args.warmup, procs=cores)
+    value, dt, cores = time_oracle_all_cores(args.steps, args.warmup, shape=crop, procs=cores)
     n1, n2, n3 = crop
     sample = (f"FP64 NumPy oracle as it stands, one Algorithm-1 pass per step on a {n1}x{n2}x{n3} "
               f"spatial crop of the workload generator in each of {cores} single-threaded processes "

@@ -67,6 +67,18 @@ def test_reference_crop_is_bounded():
         assert est <= 130 or n1 == 16
 
 
+def test_reference_crop_fits_the_memory():
+    """The crop is cut so that one oracle process per core fits in 60 % of
+    the available memory (8 processes of a 352x352x224 crop would need about
+    110 GB)."""
+    for procs, avail in ((8, 62e9), (16, 62e9), (16, 400e9), (1, 4e9)):
+        n1, n2, n3 = bench.reference_crop(3, 3, procs=procs, avail=avail)
+        assert n1 == n2 and 16 <= n1 <= 512 and n1 % 16 == 0 and n3 == 224
+        assert procs * n1 * n2 * n3 * bench.ORACLE_BYTES_PER_VOXEL <= 0.6 * avail or n1 == 16
+    # enough memory: the time budget alone decides
+    assert bench.reference_crop(3, 3, procs=1, avail=1e15) == bench.reference_crop(3, 3, procs=1, avail=0)
+
+
 def test_oracle_timing_runs_on_a_small_crop():
     value, dt = bench.time_oracle(1, 0, shape=(16, 16, 8))
     assert value > 0 and dt > 0
